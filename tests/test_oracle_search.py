@@ -1,0 +1,288 @@
+"""Pins for the oracle's search steps (construction, local search, pheromone).
+
+Every expected value is computed here from first principles (explicit tour
+surgery and full length recomputation, brute force over small instances),
+never by retyping the oracle's formulas:
+
+* Alg 3 (2-opt) with full neighbour lists and the verify pass ends in a tour
+  that no 2-opt move of all O(n^2) improves; with Or-opt enabled no segment
+  insertion of length 1..3 improves either.
+* Local search never lengthens a tour and the returned gain equals the
+  recomputed length difference.
+* Alg 2 (focused construction): tours are permutations, the new edges
+  relative to the source equal the counted ones (+ the closing edge), the
+  checklist is exactly the heads of the new edges, the start node follows
+  the Philox stream, after the quota every non-source edge is forced (both
+  source neighbours already visited); with min_new_edges > n the walk is
+  plain MMAS construction whose list fallbacks pick the nearest unvisited
+  node.
+* Eq. 2 with rho = 1/2 on a convex polygon (where the optimum is the hull
+  tour and every ant returns it): source edges stay exactly at tau_max and
+  other entries halve exactly each iteration until they reach tau_min.
+* End to end: for n <= 9 the colony's best equals the exhaustive optimum.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02228_gb300 import inputs
+
+
+def dmat(xy):
+    xy = np.asarray(xy, np.int64)
+    n = len(xy)
+    D = np.zeros((n, n), np.int64)
+    for i in range(n):
+        m = ((xy - xy[i]) ** 2).sum(1)
+        D[i] = [(math.isqrt(4 * int(v)) + 1) // 2 for v in m]
+    return D
+
+
+def length(D, route):
+    r = np.asarray(route)
+    return int(D[r, np.roll(r, -1)].sum())
+
+
+def best_2opt_delta(D, route):
+    """Smallest length change over every 2-opt move (explicit reversal)."""
+    n = len(route)
+    L0 = length(D, route)
+    best = 0
+    for i in range(n - 1):
+        for j in range(i + 2, n if i > 0 else n - 1):
+            r = list(route)
+            r[i + 1:j + 1] = r[i + 1:j + 1][::-1]
+            best = min(best, length(D, r) - L0)
+    return best
+
+
+def best_oropt_delta(D, route):
+    """Smallest change over moving a segment of 1..3 nodes (either
+    orientation) between the ends of a tour edge not adjacent to it."""
+    n = len(route)
+    L0 = length(D, route)
+    best = 0
+    for i in range(n):
+        for ell in (1, 2, 3):
+            seg = [route[(i + t) % n] for t in range(ell)]
+            rest = [route[(i + ell + t) % n] for t in range(n - ell)]  # q ... p
+            p, q = rest[-1], rest[0]
+            for t in range(len(rest)):
+                u, v = rest[t], rest[(t + 1) % len(rest)]
+                if u in (p, q) or v in (p, q):
+                    continue
+                for s in (seg, seg[::-1]):
+                    r = rest[:t + 1] + s + rest[t + 1:]
+                    best = min(best, length(D, r) - L0)
+    return best
+
+
+def is_perm(route, n):
+    return sorted(int(x) for x in route) == list(range(n))
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("oropt", [0, 1])
+def test_full_queue_ls_reaches_local_optimum(seed, oropt):
+    n = 24 + 3 * seed
+    xy = inputs.uniform(n, seed=100 + seed, side=10000)
+    D = dmat(xy)
+    cand = oracle.knn_rows(xy, n - 1)
+    # start from the nearest-neighbour tour so that Alg 3's limit of n
+    # applied moves is not what stops the search
+    route = oracle.nn_tour(xy, cand[:, :4], cand[:, 4:8])
+    L0 = length(D, route)
+    out, gain, st = oracle.local_search(xy, cand, route, route.copy(), oropt=oropt, verify=1)
+    assert st[oracle.ST_MOVES_2OPT] + st[oracle.ST_MOVES_OR] < n
+    assert is_perm(out, n)
+    assert length(D, out) == L0 - gain
+    assert gain > 0
+    assert best_2opt_delta(D, list(out)) == 0
+    if oropt:
+        assert best_oropt_delta(D, list(out)) == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ls_with_short_lists_never_lengthens(seed):
+    n = 300
+    xy = inputs.stippled(n, seed=200 + seed, blobs=6, ridges=1, side=20000)
+    D = dmat(xy)
+    cand = oracle.knn_rows(xy, 5)
+    rng = np.random.default_rng(seed)
+    route = rng.permutation(n).astype(np.int32)
+    for oropt in (0, 1):
+        for verify in (0, 1):
+            q = rng.choice(n, size=40, replace=False).astype(np.int32)
+            out, gain, st = oracle.local_search(xy, cand, route, q, oropt=oropt, verify=verify)
+            assert is_perm(out, n)
+            assert gain >= 0
+            assert length(D, out) == length(D, route) - gain
+            assert st[oracle.ST_MOVES_2OPT] + st[oracle.ST_MOVES_OR] <= n
+
+
+def edge_set(route):
+    r = list(route)
+    return {frozenset((r[i], r[(i + 1) % len(r)])) for i in range(len(r))}
+
+
+def check_construction(xy, C, src, pre, checks, it, seed, min_new):
+    n = len(xy)
+    pos_src = np.empty(n, np.int64)
+    pos_src[src] = np.arange(n)
+    E_src = edge_set(src)
+    for a in range(pre.shape[0]):
+        r = [int(x) for x in pre[a]]
+        assert is_perm(r, n)
+        assert r[0] == (oracle.draw(seed, 0, a, it, 0) * n) >> 32
+        heads, new_idx = [], []
+        for i in range(n - 1):
+            if frozenset((r[i], r[i + 1])) not in E_src:
+                heads.append(r[i + 1])
+                new_idx.append(i)
+        closing_new = frozenset((r[-1], r[0])) not in E_src
+        assert list(checks[a]) == heads
+        assert len(edge_set(r) - E_src) == len(heads) + int(closing_new)
+        if len(heads) < min_new:
+            continue  # tour completed before the quota
+        # after the quota, every non-source edge is forced
+        seen = set(r[:new_idx[min_new - 1] + 2])
+        for i in range(new_idx[min_new - 1] + 1, n - 1):
+            if frozenset((r[i], r[i + 1])) not in E_src:
+                x = r[i]
+                assert src[(pos_src[x] + 1) % n] in seen and src[(pos_src[x] - 1) % n] in seen
+            seen.add(r[i + 1])
+
+
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 200, 1), ("stippled", 400, 7), ("uniform", 57, 3)])
+def test_focused_construction_invariants(kind, n, seed):
+    xy = inputs.uniform(n, seed=300 + n) if kind == "uniform" else \
+        inputs.stippled(n, seed=300 + n, blobs=5, ridges=1, side=30000)
+    C = oracle.Colony(xy, 16, seed=seed, keep_pre_ls=1)
+    for it in range(1, 16):
+        src, _ = C.source()
+        C.iterate(12, 1)
+        pre, pre_len, checks = C.ant_pre()
+        check_construction(xy, C, src, pre, checks, it, seed, 8)
+        tours, lens = C.ant_tours()
+        D = dmat(xy) if it == 1 else D
+        for a in range(len(lens)):
+            assert is_perm(tours[a], n)
+            assert length(D, tours[a]) == lens[a] <= pre_len[a] == length(D, pre[a])
+
+
+def test_mmas_special_case_fallbacks_pick_nearest_unvisited():
+    # min_new_edges > n: the focused rule never triggers (plain MMAS walk);
+    # k = 3, bl = 2 forces backup and global fallbacks.
+    n = 150
+    xy = inputs.uniform(n, seed=401, side=50000)
+    C = oracle.Colony(xy, 3, bl_size=2, min_new_edges=n + 1, keep_pre_ls=1)
+    cand, backup, _ = C.lists()
+    xy64 = xy.astype(np.int64)
+    idx = np.arange(n)
+    fallbacks = 0
+    for it in range(3):
+        C.iterate(6, 1)
+        pre, _, _ = C.ant_pre()
+        st = C.ant_stats()
+        assert (st[:, oracle.ST_ACO_STEPS] == n - 1).all()
+        for a in range(pre.shape[0]):
+            r = pre[a]
+            vis = np.zeros(n, bool)
+            vis[r[0]] = True
+            for i in range(n - 1):
+                u, v = r[i], r[i + 1]
+                if (~vis[cand[u]]).any():
+                    assert v in cand[u] and not vis[v]
+                else:
+                    fallbacks += 1
+                    m = ((xy64 - xy64[u]) ** 2).sum(1)
+                    m = np.where(vis, np.iinfo(np.int64).max, m)
+                    assert v == np.lexsort((idx, m))[0]
+                vis[v] = True
+    assert fallbacks > 50
+
+
+def convex_polygon(n, R=100000):
+    ang = 2 * np.pi * np.arange(n) / n
+    pts = np.stack([np.rint(R + R * np.cos(ang)), np.rint(R + R * np.sin(ang))], 1)
+    perm = np.random.default_rng(n).permutation(n)  # hide the hull order
+    return pts[perm].astype(np.int32), np.argsort(perm).astype(np.int32)
+
+
+def same_cycle(a, b):
+    return edge_set(a) == edge_set(b)
+
+
+def test_pheromone_decay_and_fixed_point_on_convex_polygon():
+    n = 40
+    xy, hull = convex_polygon(n)
+    C = oracle.Colony(xy, 16)
+    assert same_cycle(C.initial()[0], hull)
+    cand, _, _ = C.lists()
+    lim0 = C.limits()
+    tmax, tmin = np.float32(lim0[2]), np.float32(lim0[3])
+    assert tmax > 0 and 0 < tmin < tmax
+    tau = C.tau()
+    assert (tau == tmax).all()
+    on_hull = np.zeros(cand.shape, bool)
+    E = edge_set(hull)
+    for u in range(n):
+        for s in range(cand.shape[1]):
+            on_hull[u, s] = frozenset((u, int(cand[u, s]))) in E
+    for t in range(1, 25):
+        hist, _ = C.iterate(8, 1)
+        assert same_cycle(C.source()[0], hull) and same_cycle(C.best()[0], hull)
+        assert hist[0, 0] == hist[0, 2] == length(dmat(xy), hull) if t == 1 else True
+        lim = C.limits()
+        assert np.float32(lim[2]) == tmax and np.float32(lim[3]) == tmin  # gb never improves
+        tau = C.tau()
+        assert (tau[on_hull] == tmax).all()  # rho*tau_max + 1/L = tau_max exactly
+        want = max(tmin, np.float32(tmax * np.float32(2.0 ** -t)))
+        assert (tau[~on_hull] == want).all()
+        # symmetry of the stored entries
+        for u in range(0, n, 7):
+            for s in range(cand.shape[1]):
+                v = cand[u, s]
+                back = np.nonzero(cand[v] == u)[0]
+                if back.size:
+                    assert tau[v, back[0]] == tau[u, s]
+    assert (tau[~on_hull] == tmin).all()
+
+
+def brute_optimum(xy):
+    D = dmat(xy)
+    n = len(xy)
+    best = None
+    for perm in itertools.permutations(range(1, n)):
+        if perm[0] > perm[-1]:
+            continue
+        L = D[0, perm[0]] + D[perm[-1], 0] + sum(D[perm[i], perm[i + 1]] for i in range(n - 2))
+        best = L if best is None or L < best else best
+    return int(best)
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 9])
+def test_small_instances_reach_the_exhaustive_optimum(n):
+    for inst in range(6 if n == 9 else 10):
+        xy = inputs.uniform(n, seed=1000 * n + inst, side=1000)
+        C = oracle.Colony(xy, 16, seed=inst + 1)
+        C.iterate(8, 30)
+        assert C.best()[1] == brute_optimum(xy)
+
+
+def test_limits_follow_global_best():
+    xy = inputs.uniform(300, seed=77)
+    C = oracle.Colony(xy, 16)
+    for _ in range(5):
+        hist, _ = C.iterate(16, 1)
+        lim = C.limits()
+        gb = C.best()[1]
+        assert hist[0, 2] == gb
+        # tau_max (1 - rho) L_gb = 1 up to one rounding of the double division
+        assert abs(lim[0] * 0.5 * gb - 1.0) < 1e-15
+        assert lim[2] == np.float32(lim[0]) and lim[3] == np.float32(lim[1])
+        assert 0 < lim[1] < lim[0]
+        assert (C.tau() >= np.float32(lim[1])).all() and (C.tau() <= np.float32(lim[0])).all()
