@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark: Focused ACO on the n = 100,000 stippled workload (1,024 ants,
+100 iterations, k = 16, Philox seed 1) on GB300.
+
+One step = one full solve of that instance through the library: colony
+set-up from device-resident coordinates (candidate/backup lists, initial
+tour), 100 iterations of 1,024 ants (focused construction + local search +
+colony update), and the global-best tour copied to a device buffer.
+
+  value     ant-solutions per second of the whole job (ants * iterations *
+            ranks / step time), CUDA events on the colony's stream;
+  e2e       the same metric through the public host API (faco_create_ex from
+            pinned host coordinates, faco_iterate, faco_best into a host
+            array), host<->device copies inside the timed region;
+  roofline  the per-ant kernel (construction + local search), timed live
+            with CUDA events around each launch; achieved = algorithmic
+            bytes / kernel time against the measured HBM copy bandwidth;
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+
+L2 is flushed (a 512 MB write) before every timed step.  Under torchrun each
+rank solves its own copy of the instance (independent colonies, no data-path
+collective): weak scaling.
+
+--impl reference times the CPU oracle instead (the method's plain
+statement, test infrastructure) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ant-solutions/sec at 100k nodes"
+UNIT = "ant-solutions/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def host_cores() -> int:
+    return os.cpu_count() or 1
+
+
+def oracle_sample(xy, ants, iters, k, sample_ants, sample_iters, threads):
+    """Times the oracle's set-up and `sample_iters` iterations of
+    `sample_ants` ants; returns the full-job throughput implied by them."""
+    import oracle
+
+    t0 = time.perf_counter()
+    col = oracle.Colony(xy, k, threads=threads)
+    t_create = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    col.iterate(sample_ants, sample_iters)
+    t_iter = (time.perf_counter() - t0) / (sample_iters * sample_ants)  # seconds per ant-solution
+    col.close()
+    t_job = t_create + t_iter * ants * iters
+    return ants * iters / t_job, t_create, t_iter
+
+
+def run_reference(args, W):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    from paper_2203_02228_gb300 import inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    xy = inputs.workload_points(args.workload)
+    threads = host_cores()
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, tc, ti = oracle_sample(xy, W["ants"], W["iters"], 16, args.ref_ants, 1, threads)
+        if s >= args.warmup:
+            vals.append(v)
+    v = statistics.mean(vals)
+    sample = ("per step: oracle set-up of the full instance + 1 iteration of %d ants; value = "
+              "ants*iterations / (set-up + per-ant time * %d ants * %d iterations)") % (
+        args.ref_ants, W["ants"], W["iters"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": W["ants"] * W["iters"] / v * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+int64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": W["n"], "ants": W["ants"], "iterations": W["iters"],
+                   "k": 16, "seed": 1},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="faco", choices=["faco", "reference"])
+    ap.add_argument("--workload", default="stippled100k")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-ants", type=int, default=32)
+    ap.add_argument("--iters", type=int, default=0, help="override the iteration budget (testing only)")
+    args = ap.parse_args()
+
+    from paper_2203_02228_gb300 import inputs
+
+    W = dict(inputs.WORKLOADS[args.workload])
+    if args.iters:
+        W["iters"] = args.iters
+    if args.impl == "reference":
+        return run_reference(args, W)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_02228_gb300 import Colony, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    xy = inputs.workload_points(args.workload)
+    n, ants, iters = xy.shape[0], W["ants"], W["iters"]
+    xy_dev = torch.from_numpy(xy).to(dev)
+    tour_dev = torch.empty(n, dtype=torch.int32, device=dev)
+    len_dev = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def solve(profile=False):
+        col = Colony(xy_dev, 16, device=True, stream=stream)
+        if profile:
+            col.profile(True)
+        col.iterate(ants, iters)
+        col.best_device(tour_dev, len_dev)
+        st = col.stats()
+        prof = col.profile_read() if profile else (0.0, 0)
+        col.close()
+        return st, prof
+
+    for _ in range(args.warmup):
+        solve()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms = []
+    ants_ms = 0.0
+    ants_launches = 0
+    algo_bytes = 0
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, (pms, pcnt) = solve(profile=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ants_ms += pms
+        ants_launches += pcnt
+        launches += st.kernel_launches
+        # algorithmic bytes of the per-ant kernel: explicit route+pos per ant
+        # (16n), source rows per roulette step (2 x 64 B + visited/route 16 B),
+        # 16 B per reversed element, 2k x 20 B per local-search pop.
+        algo_bytes += (16 * n * ants * iters + 208 * st.aco_steps + 16 * st.flip_elems + 640 * st.ls_pops)
+    barrier()
+    clk = clocks.stop()
+
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ants * iters * world / (ms / 1e3)
+
+    # end to end through the host API (pinned host coordinates, host tour)
+    e2e = None
+    if not args.no_e2e:
+        from paper_2203_02228_gb300 import _lib, faco_best, faco_create_ex, faco_destroy, faco_iterate
+        pinned = torch.from_numpy(xy).pin_memory()
+        tour_host = np.zeros(n, np.int32)
+        p = _lib.params_default()
+        p.stream = stream.cuda_stream
+        e2e_ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            h = faco_create_ex(pinned, n, 16, p)
+            faco_iterate(h, ants, iters)
+            faco_best(h, tour_host, n)
+            t1 = time.perf_counter()
+            faco_destroy(h)
+            e2e_ms.append((t1 - t0) * 1e3)
+        em = statistics.mean(e2e_ms)
+        if world > 1:
+            t = torch.tensor([em], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            em = float(t.item())
+        e2e = {"value": ants * iters * world / (em / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 4 * n + 8, "ms_per_step": em}
+
+    peak, peak_src = load_peaks()
+    achieved = (algo_bytes / ants_launches) / (ants_ms / ants_launches / 1e3) / 1e9 if ants_launches else None
+    roofline = {"kernel": "k_ants (construction + local search)", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "avg_launch_ms": ants_ms / ants_launches if ants_launches else None,
+                "algorithmic_bytes_per_launch": algo_bytes / ants_launches if ants_launches else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, tc, ti = oracle_sample(xy, ants, iters, 16, 32, 1, host_cores())
+        cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": "oracle set-up of the full instance (%.1f s) + 1 iteration of 32 ants (%.1f ms per "
+                         "ant-solution), extrapolated to %d ants x %d iterations" % (tc, ti * 1e3, ants, iters)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "ants": ants, "iterations": iters, "k": 16,
+                       "seed": 1, "l2": "flushed before every step (512 MB write)",
+                       "parallelism": "independent colonies per rank" if world > 1 else "single colony"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

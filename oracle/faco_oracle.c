@@ -503,7 +503,7 @@ static int32_t select_next(const orc_colony* C, int32_t u, const uint8_t* visite
     w[s] = 0.0f;
     if (s < k && !visited[C->cand[(size_t)u * k + s]]) {
       w[s] = C->tau[(size_t)u * k + s] * C->eta[(size_t)u * k + s];
-      any = 1;
+      if (w[s] > 0.0f) any = 1; /* tau >= tau_min > 0 and eta > 0 */
     }
   }
   if (any) {

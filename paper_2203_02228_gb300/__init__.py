@@ -1,0 +1,218 @@
+"""GB300-native Focused ACO (Skinderowicz, Applied Soft Computing 2022).
+
+Python face of libfaco.so (C ABI in include/faco.h).  The functions keep the
+C names (faco_create, faco_iterate, faco_best, ...); ``Colony`` bundles them
+for one instance.  PyTorch is only used, when given, for the CUDA stream and
+for device-resident input/output buffers.
+
+    from paper_2203_02228_gb300 import Colony, inputs
+    col = Colony(inputs.uniform(1000), k=16)
+    col.iterate(ants=32, budget=200)
+    tour, length = col.best()
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FacoError, faco_params, faco_stats, load, params_default  # noqa: F401
+
+__all__ = ["Colony", "FacoError", "faco_params", "faco_stats", "load", "params_default",
+           "faco_create", "faco_create_ex", "faco_create_device", "faco_iterate", "faco_sync",
+           "faco_best", "faco_best_device", "faco_stats_get", "faco_destroy", "faco_strerror"]
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---- C ABI, same names ---------------------------------------------------
+
+def faco_create(coords_xy: np.ndarray, n: int, k: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _lib.check(load().faco_create(_ptr(coords_xy), n, k, ctypes.byref(h)), "faco_create")
+    return h
+
+
+def faco_create_ex(coords_xy: np.ndarray, n: int, k: int, params: faco_params | None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _lib.check(load().faco_create_ex(_ptr(coords_xy), n, k, p, ctypes.byref(h)), "faco_create_ex")
+    return h
+
+
+def faco_create_device(coords_xy_dev, n: int, k: int, params: faco_params | None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _lib.check(load().faco_create_device(_ptr(coords_xy_dev), n, k, p, ctypes.byref(h)), "faco_create_device")
+    return h
+
+
+def faco_iterate(h, ants: int, budget: int) -> None:
+    _lib.check(load().faco_iterate(h, ants, budget), "faco_iterate")
+
+
+def faco_sync(h) -> None:
+    _lib.check(load().faco_sync(h), "faco_sync")
+
+
+def faco_best(h, tour: np.ndarray | None, length: int) -> int:
+    L = ctypes.c_int64()
+    _lib.check(load().faco_best(h, _ptr(tour), length, ctypes.byref(L)), "faco_best")
+    return int(L.value)
+
+
+def faco_best_device(h, tour_dev, length_dev) -> None:
+    _lib.check(load().faco_best_device(h, _ptr(tour_dev), _ptr(length_dev)), "faco_best_device")
+
+
+def faco_stats_get(h) -> faco_stats:
+    s = faco_stats()
+    _lib.check(load().faco_stats_get(h, ctypes.byref(s)), "faco_stats_get")
+    return s
+
+
+def faco_destroy(h) -> None:
+    load().faco_destroy(h)
+
+
+def faco_strerror(status: int) -> str:
+    return _lib.strerror(status)
+
+
+# ---- convenience wrapper -------------------------------------------------
+
+class Colony:
+    """One FACO colony on the GPU (all state resident on the device)."""
+
+    def __init__(self, coords, k: int = 16, params: faco_params | None = None, device: bool = False,
+                 stream=None, **kw):
+        p = params if params is not None else params_default()
+        for key, v in kw.items():
+            setattr(p, key, v)
+        if stream is not None:
+            p.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.params = p
+        self._L = load()
+        if device:
+            n = int(coords.shape[0])
+            self._h = faco_create_device(coords, n, k, p)
+        else:
+            coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)
+            n = coords.shape[0]
+            self._h = faco_create_ex(coords, n, k, p)
+        st = self.stats()
+        self.n, self.k, self.bl = st.n, st.k, st.bl
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            faco_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def iterate(self, ants: int, budget: int = 1) -> None:
+        faco_iterate(self._h, ants, budget)
+
+    def sync(self) -> None:
+        faco_sync(self._h)
+
+    def best(self):
+        tour = np.zeros(self.n, np.int32)
+        L = faco_best(self._h, tour, self.n)
+        return tour, L
+
+    def best_device(self, tour_dev, length_dev) -> None:
+        faco_best_device(self._h, tour_dev, length_dev)
+
+    def stats(self) -> faco_stats:
+        return faco_stats_get(self._h)
+
+    def lists(self):
+        cand = np.zeros((self.n, self.k), np.int32)
+        backup = np.zeros((self.n, max(self.bl, 1)), np.int32)
+        eta = np.zeros((self.n, self.k), np.float32)
+        _lib.check(self._L.faco_get_lists(self._h, _ptr(cand), _ptr(backup), _ptr(eta)), "faco_get_lists")
+        return cand, backup[:, :self.bl], eta
+
+    def tau(self) -> np.ndarray:
+        t = np.zeros((self.n, self.k), np.float32)
+        _lib.check(self._L.faco_get_tau(self._h, _ptr(t)), "faco_get_tau")
+        return t
+
+    def limits(self) -> np.ndarray:
+        out = np.zeros(4, np.float64)
+        _lib.check(self._L.faco_get_limits(self._h, _ptr(out)), "faco_get_limits")
+        return out
+
+    def _route(self, fn, what):
+        r = np.zeros(self.n, np.int32)
+        L = ctypes.c_int64()
+        _lib.check(fn(self._h, _ptr(r), ctypes.byref(L)), what)
+        return r, int(L.value)
+
+    def source(self):
+        return self._route(self._L.faco_get_source, "faco_get_source")
+
+    def initial(self):
+        return self._route(self._L.faco_get_initial, "faco_get_initial")
+
+    def history(self, max_iters: int = 1 << 20) -> np.ndarray:
+        st = self.stats()
+        m = min(max_iters, st.iteration)
+        h = np.zeros((max(m, 1), 4), np.int64)
+        rows = ctypes.c_int64()
+        _lib.check(self._L.faco_get_history(self._h, _ptr(h), m, ctypes.byref(rows)), "faco_get_history")
+        return h[:rows.value]
+
+    def profile(self, on: bool = True) -> None:
+        _lib.check(self._L.faco_profile_enable(self._h, int(on)), "faco_profile_enable")
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _lib.check(self._L.faco_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "faco_profile_read")
+        return float(ms.value), int(cnt.value)
+
+    def ant_tours(self):
+        m = self.stats().ants
+        t = np.zeros((m, self.n), np.int32)
+        lens = np.zeros(m, np.int64)
+        _lib.check(self._L.faco_get_ant_tours(self._h, _ptr(t), _ptr(lens)), "faco_get_ant_tours")
+        return t, lens
+
+    def ant_pre(self):
+        m = self.stats().ants
+        t = np.zeros((m, self.n), np.int32)
+        lens = np.zeros(m, np.int64)
+        chk = np.zeros((m, self.n), np.int32)
+        nchk = np.zeros(m, np.int32)
+        _lib.check(self._L.faco_get_ant_pre(self._h, _ptr(t), _ptr(lens), _ptr(chk), _ptr(nchk)),
+                   "faco_get_ant_pre")
+        return t, lens, [chk[i, :nchk[i]].copy() for i in range(m)]
+
+
+def device_selftest(what: int, inp: np.ndarray, out: np.ndarray, count: int, width: int = 16, seed: int = 0) -> None:
+    """Runs a device primitive through the library (see faco_test_device)."""
+    _lib.check(load().faco_test_device(what, _ptr(inp), inp.nbytes, _ptr(out), out.nbytes, count, width, seed),
+               "faco_test_device")

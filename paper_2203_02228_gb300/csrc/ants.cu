@@ -1,0 +1,414 @@
+// ants.cu -- one warp per ant: focused tour construction (Sec. 4.3, Alg 2)
+// followed by the checklist-seeded local search (Sec. 4.4, Alg 3).
+//
+// Construction works in the SOURCE solution's position space: the colony
+// keeps, per iteration, the candidate rows re-ordered by source position
+// (Wsrc = tau*eta, Csrc = the candidates' source positions), so that an ant
+// walking along the source reads consecutive rows, and the visited set is a
+// bit per source position (shared memory).  Because the pheromone contrast
+// makes the roulette follow the source edge almost always, a warp evaluates
+// the next 32 roulette steps speculatively, one per lane: lane t assumes the
+// ant reached p_t = pc + t*dir by following the source, treats p_1..p_t as
+// visited, and draws its own Philox number (draw index = route index).  The
+// first lane whose pick leaves the source ends the confirmed prefix; its own
+// pick is the ant's next step.  The result equals the sequential walk step
+// for step.
+//
+// Readings (shared with the oracle, decided there independently):
+//   start node   floor(x * n / 2^32) of draw 0;
+//   roulette     Eq. 1 with alpha = beta = 1 (see common.cuh);
+//   fallbacks    first unvisited node of the backup list, else the unvisited
+//                node nearest by (squared distance, node id);
+//   new edge     v is neither source successor nor predecessor of u;
+//   completion   once new_edges >= min_new_edges: copy the source forward
+//                from the current end while unvisited, then backward while
+//                unvisited, then resume the ACO rule;
+//   checklist    the head v of every new edge, in order.
+#include "common.cuh"
+#include "launch.h"
+#include "ls_array.cuh"
+
+namespace faco {
+
+namespace {
+
+__device__ __forceinline__ bool vis_get(const uint32_t* w, int q) { return (w[q >> 5] >> (q & 31)) & 1u; }
+
+// Set visited bits for the linear range [a, b] (a <= b) with the warp.
+__device__ __forceinline__ void vis_set_linear(uint32_t* w, int a, int b) {
+  const int wa = a >> 5, wb = b >> 5;
+  for (int x = wa + lane_id(); x <= wb; x += 32) {
+    uint32_t m = 0xffffffffu;
+    if (x == wa) m &= 0xffffffffu << (a & 31);
+    if (x == wb) m &= 0xffffffffu >> (31 - (b & 31));
+    w[x] |= m;
+  }
+}
+
+// Set visited bits for the c positions pc+dir, ..., pc+c*dir (cyclic).
+__device__ __forceinline__ void vis_set_run(uint32_t* w, int n, int pc, int dir, int c) {
+  int a, b;
+  if (dir > 0) {
+    a = pc + 1;
+    b = pc + c;
+  } else {
+    a = pc - c;
+    b = pc - 1;
+  }
+  if (a < 0) {
+    vis_set_linear(w, a + n, n - 1);
+    vis_set_linear(w, 0, b);
+  } else if (b >= n) {
+    vis_set_linear(w, a, n - 1);
+    vis_set_linear(w, 0, b - n);
+  } else {
+    vis_set_linear(w, a, b);
+  }
+  __syncwarp();
+}
+
+// First visited position in [a, b) ascending, or -1.
+__device__ __forceinline__ int first_set_up(const uint32_t* w, int a, int b) {
+  if (a >= b) return -1;
+  const int wa = a >> 5, wb = (b - 1) >> 5;
+  for (int base = wa; base <= wb; base += 32) {
+    const int x = base + lane_id();
+    uint32_t m = 0;
+    if (x <= wb) {
+      m = w[x];
+      if (x == wa) m &= 0xffffffffu << (a & 31);
+      if (x == wb) m &= 0xffffffffu >> (31 - ((b - 1) & 31));
+    }
+    const unsigned bal = __ballot_sync(kFull, m != 0);
+    if (bal) {
+      const int l = __ffs(bal) - 1;
+      const uint32_t ml = __shfl_sync(kFull, m, l);
+      return (base + l) * 32 + __ffs(ml) - 1;
+    }
+  }
+  return -1;
+}
+
+// Last visited position in [a, b] descending, or -1.
+__device__ __forceinline__ int last_set_down(const uint32_t* w, int a, int b) {
+  if (a > b) return -1;
+  const int wa = a >> 5, wb = b >> 5;
+  for (int top = wb; top >= wa; top -= 32) {
+    const int x = top - lane_id();
+    uint32_t m = 0;
+    if (x >= wa) {
+      m = w[x];
+      if (x == wa) m &= 0xffffffffu << (a & 31);
+      if (x == wb) m &= 0xffffffffu >> (31 - (b & 31));
+    }
+    const unsigned bal = __ballot_sync(kFull, m != 0);
+    if (bal) {
+      const int l = __ffs(bal) - 1;
+      const uint32_t ml = __shfl_sync(kFull, m, l);
+      return (top - l) * 32 + 31 - __clz(ml);
+    }
+  }
+  return -1;
+}
+
+// Number of consecutive unvisited positions s, s+dir, s+2dir, ... (cyclic);
+// at least one position is visited, so the result is < n.
+__device__ __forceinline__ int unvisited_run(const uint32_t* w, int n, int s, int dir) {
+  if (dir > 0) {
+    int p = first_set_up(w, s, n);
+    if (p >= 0) return p - s;
+    p = first_set_up(w, 0, s);
+    return (n - s) + p;
+  }
+  int p = last_set_down(w, 0, s);
+  if (p >= 0) return s - p;
+  p = last_set_down(w, s + 1, n - 1);
+  return s + (n - p);
+}
+
+// Sum of the source edge lengths covered by a run of `len` nodes starting
+// at source position `first` and moving in direction `dir`.
+__device__ __forceinline__ int64_t run_sum(const Colony& C, int first, int dir, int len) {
+  if (len <= 1) return 0;
+  const int n = C.n, cnt = len - 1;
+  const int lo = dir > 0 ? first : wrapn(first - cnt, n);
+  const int hi = lo + cnt;
+  if (hi <= n) return C.Psrc[hi] - C.Psrc[lo];
+  return (C.Psrc[n] - C.Psrc[lo]) + C.Psrc[hi - n];
+}
+
+struct Walk {
+  int kf;          // route entries filled
+  int pc;          // source position of the current end
+  int dir;         // direction of the current run (0: single node)
+  int run_first;   // source position where the current run starts
+  int run_len;
+  int first_q;     // source position of route[0]
+  int new_edges, nchk;
+  int64_t len;     // length of the closed runs and connecting edges
+  int64_t aco, backup, global;
+};
+
+// Writes route/pos for the c positions following pc in direction dir.
+__device__ __forceinline__ void place_run(const Colony& C, int32_t* route, int32_t* pos, const Walk& W,
+                                          int dir, int c) {
+  const int n = C.n, lane = lane_id();
+  constexpr int U = 8;
+  for (int i0 = 0; i0 < c; i0 += 32 * U) {
+    int nd[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + lane + 32 * u;
+      nd[u] = -1;
+      if (i < c) nd[u] = C.src_route[wrapn(W.pc + dir * (i + 1), n)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + lane + 32 * u;
+      if (i < c) {
+        route[W.kf + i] = nd[u];
+        pos[nd[u]] = W.kf + i;
+      }
+    }
+  }
+}
+
+// Backup list, then global nearest unvisited node (warp).  Returns the
+// source position of the chosen node.
+__device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, int pc, Walk& W) {
+  const int n = C.n, lane = lane_id();
+  const int u = C.src_route[pc];
+  for (int j0 = 0; j0 < C.bl; j0 += 32) {
+    const int j = j0 + lane;
+    int q = -1;
+    if (j < C.bl) {
+      q = C.src_pos[C.backup[(size_t)u * C.bl + j]];
+      if (vis_get(vis, q)) q = -1;
+    }
+    const unsigned bal = __ballot_sync(kFull, q >= 0);
+    if (bal) {
+      W.backup++;
+      return __shfl_sync(kFull, q, __ffs(bal) - 1);
+    }
+  }
+  const int2 xu = C.XYsrc[pc];
+  uint64_t bk = ~0ull;
+  int32_t bi = INT_MAX;
+  for (int q = lane; q < n; q += 32) {
+    if (!vis_get(vis, q)) {
+      const uint64_t m = sqdist(xu, C.XYsrc[q]);
+      const int32_t node = C.src_route[q];
+      if (m < bk || (m == bk && node < bi)) {
+        bk = m;
+        bi = node;
+      }
+    }
+  }
+  warp_min_key(bk, bi);
+  W.global++;
+  if (bi < 0 || bi >= n) {  // cannot happen while a node is unvisited
+    if (lane == 0) atomicOr(&C.st->error, kErrInternal);
+    return pc == 0 ? n - 1 : pc - 1;
+  }
+  return C.src_pos[bi];
+}
+
+// One ACO step (already chosen source position q) from the current end.
+__device__ __forceinline__ void place_step(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
+                                           int32_t* chk, Walk& W, int q) {
+  const int n = C.n, lane = lane_id();
+  const int node = C.src_route[q];
+  const int up = W.pc + 1 == n ? 0 : W.pc + 1;
+  const int dn = W.pc == 0 ? n - 1 : W.pc - 1;
+  if (q != up && q != dn) {  // new edge
+    W.len += run_sum(C, W.run_first, W.dir, W.run_len) + euc2d(C.XYsrc[W.pc], C.XYsrc[q]);
+    if (lane == 0) chk[W.nchk] = node;
+    W.nchk++;
+    W.new_edges++;
+    W.run_first = q;
+    W.run_len = 1;
+    W.dir = 0;
+  } else {
+    if (W.dir == 0) W.dir = (q == up) ? 1 : -1;
+    W.run_len++;
+  }
+  if (lane == 0) {
+    route[W.kf] = node;
+    pos[node] = W.kf;
+    vis[q >> 5] |= 1u << (q & 31);
+  }
+  __syncwarp();
+  W.kf++;
+  W.pc = q;
+}
+
+// Up to `nspec` roulette steps, lane t taking the step at pc + t*dir.
+template <int KW>
+__device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
+                                          int32_t* chk, Walk& W, int nspec, uint32_t ant,
+                                          uint32_t iter) {
+  const int n = C.n, lane = lane_id();
+  const bool valid = lane < nspec && W.kf + lane < n;
+  const int pt = wrapn(W.pc + lane * W.dir, n);
+  bool any = false;
+  int q = -1;
+  if (valid) {
+    float w[KW];
+    int c[KW];
+    const float4* wr = reinterpret_cast<const float4*>(C.Wsrc + (size_t)pt * KW);
+    const int4* cr = reinterpret_cast<const int4*>(C.Csrc + (size_t)pt * KW);
+#pragma unroll
+    for (int v = 0; v < KW / 4; ++v) {
+      const float4 a = wr[v];
+      const int4 b = cr[v];
+      w[4 * v] = a.x; w[4 * v + 1] = a.y; w[4 * v + 2] = a.z; w[4 * v + 3] = a.w;
+      c[4 * v] = b.x; c[4 * v + 1] = b.y; c[4 * v + 2] = b.z; c[4 * v + 3] = b.w;
+    }
+#pragma unroll
+    for (int s = 0; s < KW; ++s) {
+      bool seen = c[s] < 0;
+      if (!seen) {
+        seen = vis_get(vis, c[s]);
+        if (!seen && W.dir != 0) {
+          int off = (c[s] - W.pc) * W.dir;
+          if (off < 0) off += n;
+          seen = off >= 1 && off <= lane;  // visited earlier in this speculative run
+        }
+      }
+      if (seen) w[s] = 0.0f;
+      any |= w[s] > 0.0f;
+    }
+    if (any) {
+      const float u = u01(draw(C.seed, (uint32_t)(W.kf + lane), ant, iter, 0));
+      q = c[roulette<KW>(w, u)];
+    }
+  }
+  const bool follows = valid && any && W.dir != 0 && q == wrapn(pt + W.dir, n);
+  const unsigned stop = __ballot_sync(kFull, !follows);
+  const int f = stop ? __ffs(stop) - 1 : 32;
+  if (f > 0) {
+    place_run(C, route, pos, W, W.dir, f);
+    vis_set_run(vis, n, W.pc, W.dir, f);
+    W.pc = wrapn(W.pc + f * W.dir, n);
+    W.run_len += f;
+    W.kf += f;
+    W.aco += f;
+  }
+  if (f < nspec && W.kf < n) {
+    const int anyf = __shfl_sync(kFull, (int)any, f);
+    int qf = __shfl_sync(kFull, q, f);
+    if (!anyf) qf = fallback_pick(C, vis, W.pc, W);
+    W.aco++;
+    place_step(C, route, pos, vis, chk, W, qf);
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
+  extern __shared__ uint32_t smem_vis[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (ant >= A.m) return;
+  const int n = C.n;
+  const int words = (n + 31) >> 5;
+  uint32_t* vis = A.smem_vis ? smem_vis + (size_t)wib * words : A.vis_g + (size_t)ant * words;
+  for (int i = lane; i < words; i += 32) vis[i] = 0;
+  __syncwarp();
+  const uint32_t iter = (uint32_t)(C.st->iter + 1);
+  int32_t* route = A.route + (size_t)ant * n;
+  int32_t* pos = A.pos + (size_t)ant * n;
+  int32_t* chk = A.chk + (size_t)ant * n;
+
+  Walk W;
+  {
+    const uint32_t x0 = draw(C.seed, 0, (uint32_t)ant, iter, 0);
+    const int s0 = (int)(((uint64_t)x0 * (uint64_t)n) >> 32);
+    const int q0 = C.src_pos[s0];
+    if (lane == 0) {
+      route[0] = s0;
+      pos[s0] = 0;
+      vis[q0 >> 5] |= 1u << (q0 & 31);
+    }
+    __syncwarp();
+    W.kf = 1; W.pc = q0; W.dir = 0; W.run_first = q0; W.run_len = 1; W.first_q = q0;
+    W.new_edges = 0; W.nchk = 0; W.len = 0; W.aco = 0; W.backup = 0; W.global = 0;
+  }
+  while (W.kf < n) {
+    if (W.new_edges >= C.min_new_edges) {
+      // complete along the source: forward, then backward
+      int c = unvisited_run(vis, n, W.pc + 1 == n ? 0 : W.pc + 1, 1);
+      if (c > 0) {
+        if (W.dir == 0) W.dir = 1;
+        place_run(C, route, pos, W, 1, c);
+        vis_set_run(vis, n, W.pc, 1, c);
+        W.pc = wrapn(W.pc + c, n);
+        W.run_len += c;
+        W.kf += c;
+      }
+      c = unvisited_run(vis, n, W.pc == 0 ? n - 1 : W.pc - 1, -1);
+      if (c > 0) {
+        if (W.dir == 0) W.dir = -1;
+        place_run(C, route, pos, W, -1, c);
+        vis_set_run(vis, n, W.pc, -1, c);
+        W.pc = wrapn(W.pc - c, n);
+        W.run_len += c;
+        W.kf += c;
+      }
+      if (W.kf >= n) break;
+      aco_steps<KW>(C, route, pos, vis, chk, W, 1, (uint32_t)ant, iter);
+    } else {
+      aco_steps<KW>(C, route, pos, vis, chk, W, W.dir != 0 ? 32 : 1, (uint32_t)ant, iter);
+    }
+  }
+  const int64_t pre_len = W.len + run_sum(C, W.run_first, W.dir, W.run_len) +
+                          euc2d(C.XYsrc[W.pc], C.XYsrc[W.first_q]);
+  __syncwarp();
+  if (A.pre_route) {
+    for (int i = lane; i < n; i += 32) A.pre_route[(size_t)ant * n + i] = route[i];
+    for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = chk[i];
+    if (lane == 0) {
+      A.pre_len[ant] = pre_len;
+      A.pre_nchk[ant] = W.nchk;
+    }
+  }
+  // local search seeded with the checklist
+  LsEnv E;
+  E.n = n; E.k = C.k; E.oropt = C.oropt; E.verify = C.verify; E.xy = C.xy; E.cand = C.cand;
+  E.queue = A.queue + (size_t)ant * n;
+  E.flags = A.flags + (size_t)ant * n;
+  E.logb = A.logb + (size_t)ant * n;
+  ArrTour T{n, route, pos};
+  LsStats S{0, 0, 0, 0, 0};
+  const int64_t gain = ls_array_run(E, T, chk, W.nchk, S);
+  if (lane == 0) {
+    A.len[ant] = pre_len - gain;
+    int64_t* st = A.stats + (size_t)ant * kNStats;
+    // counters accumulate over iterations (zeroed when the ant buffers are made)
+    st[kStAco] += W.aco; st[kStNew] += W.new_edges; st[kStBackup] += W.backup;
+    st[kStGlobal] += W.global; st[kStCheck] += W.nchk; st[kStPops] += S.pops;
+    st[kStMoves2] += S.moves2; st[kStMovesOr] += S.movesor; st[kStFlip] += S.flip;
+    st[kStVerify] += S.verify;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s) {
+  const int warps = 4;
+  const int words = (C.n + 31) >> 5;
+  const size_t smem = A.smem_vis ? (size_t)warps * words * sizeof(uint32_t) : 0;
+  const dim3 grid((A.m + warps - 1) / warps), block(32 * warps);
+  if (C.kw == 16) {
+    k_ants<16><<<grid, block, smem, s>>>(C, A);
+  } else {
+    k_ants<32><<<grid, block, smem, s>>>(C, A);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_ants_kernel(int kw, size_t smem) {
+  if (kw == 16) return cudaFuncSetAttribute(k_ants<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_ants<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace faco

@@ -1,0 +1,249 @@
+// colony.cu -- per-iteration colony kernels of Alg 2 after the ants:
+// iteration best and global best with the trail limits of Sec. 4.5, the
+// source choice (global best with probability p_source_gb, Sec. 5.2),
+// the pheromone update of Eq. 2 on candidate edges (Sec. 4.2), and the
+// source-ordered rows that the next iteration's ants read.
+#include "common.cuh"
+#include "launch.h"
+
+namespace faco {
+
+namespace {
+
+// Eq. 2 for every stored entry of the node at source position p, fused with
+// the emission of that node's row in source order for the next iteration:
+//   tau' = max(tau_min, min(tau_max, fmaf(rho, tau, delta * [edge in source])))
+//   Wsrc[p][s] = tau' * eta,  Csrc[p][s] = source position of cand[u][s].
+// update = 0 only sets tau = tau_max (Alg 2 set-up).
+__global__ void k_rows(Colony C, int update) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = C.n;
+  if (p >= n) return;
+  const int u = C.src_route[p];
+  const int pn = C.src_route[p + 1 == n ? 0 : p + 1];
+  const int pp = C.src_route[p == 0 ? n - 1 : p - 1];
+  const float tmax = C.st->tmax, tmin = C.st->tmin, delta = C.st->delta;
+  const int k = C.k, kw = C.kw;
+  for (int s = 0; s < k; ++s) {
+    const size_t idx = (size_t)u * k + s;
+    const int v = C.cand[idx];
+    float t;
+    if (update) {
+      const float dep = (v == pn || v == pp) ? delta : 0.0f;
+      t = __fmaf_rn(C.rho, C.tau[idx], dep);
+      t = t < tmax ? t : tmax;
+      t = t > tmin ? t : tmin;
+    } else {
+      t = tmax;
+    }
+    C.tau[idx] = t;
+    C.Wsrc[(size_t)p * kw + s] = __fmul_rn(t, C.eta[idx]);
+    C.Csrc[(size_t)p * kw + s] = C.src_pos[v];
+  }
+  for (int s = k; s < kw; ++s) {
+    C.Wsrc[(size_t)p * kw + s] = 0.0f;
+    C.Csrc[(size_t)p * kw + s] = -1;
+  }
+  const int2 xu = C.xy[u];
+  C.XYsrc[p] = xu;
+  C.Dsrc[p] = euc2d(xu, C.xy[pn]);
+}
+
+// Exclusive prefix sums of the source edge lengths (one block).
+__global__ void __launch_bounds__(1024) k_scan_P(Colony C) {
+  __shared__ int64_t warp_tot[32];
+  const int n = C.n, t = threadIdx.x, T = blockDim.x;
+  const int chunk = (n + T - 1) / T;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int64_t s = 0;
+  for (int i = lo; i < hi; ++i) s += C.Dsrc[i];
+  // block exclusive scan of s
+  const int lane = t & 31, w = t >> 5;
+  int64_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = shfl64_up(incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t v = lane < (T >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = shfl64_up(v, o);
+      if (lane >= o) v += y;
+    }
+    warp_tot[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  int64_t run = (incl - s) + (w > 0 ? warp_tot[w - 1] : 0);
+  for (int i = lo; i < hi; ++i) {
+    C.Psrc[i] = run;
+    run += C.Dsrc[i];
+  }
+  if (t == T - 1) C.Psrc[n] = warp_tot[(T >> 5) - 1];
+}
+
+__device__ __forceinline__ void set_limits(const Colony& C, DevState* st, int64_t L) {
+  st->tmax_d = 1.0 / ((double)L * (1.0 - (double)C.rho));
+  st->tmin_d = st->tmax_d * C.c_min;
+  st->tmax = __double2float_rn(st->tmax_d);
+  st->tmin = __double2float_rn(st->tmin_d);
+}
+
+// Iteration best (shortest, lowest ant on ties), global best + limits,
+// source choice, deposit amount, history row (one block).
+__global__ void __launch_bounds__(1024) k_best(Colony C, Ants A) {
+  __shared__ int64_t sl[32];
+  __shared__ int32_t sa[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int64_t bl = INT64_MAX;
+  int32_t ba = INT32_MAX;
+  for (int a = t; a < A.m; a += blockDim.x) {
+    const int64_t L = A.len[a];
+    if (L < bl || (L == bl && a < ba)) {
+      bl = L;
+      ba = a;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t l2 = shfl64_xor(bl, o);
+    const int32_t a2 = __shfl_xor_sync(kFull, ba, o);
+    if (l2 < bl || (l2 == bl && a2 < ba)) {
+      bl = l2;
+      ba = a2;
+    }
+  }
+  if (lane == 0) {
+    sl[w] = bl;
+    sa[w] = ba;
+  }
+  __syncthreads();
+  if (t != 0) return;
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+    if (sl[i] < bl || (sl[i] == bl && sa[i] < ba)) {
+      bl = sl[i];
+      ba = sa[i];
+    }
+  DevState* st = C.st;
+  const int64_t iter = st->iter + 1;
+  const int improved = bl < st->gb_len;
+  if (improved) {
+    st->gb_len = bl;
+    set_limits(C, st, bl);
+  }
+  const float u = u01(draw(C.seed, 0, 0, (uint32_t)iter, 1));
+  const int use_gb = (double)u < C.p_src_gb;
+  st->src_len = use_gb ? st->gb_len : bl;
+  st->delta = __double2float_rn(1.0 / (double)st->src_len);
+  st->it_best_len = bl;
+  st->it_best_ant = ba;
+  st->gb_improved = improved;
+  st->use_gb = use_gb;
+  st->iter = iter;
+  if (iter - 1 < st->hist_cap) {
+    int64_t* h = st->hist + 4 * (iter - 1);
+    h[0] = bl;
+    h[1] = ba;
+    h[2] = st->gb_len;
+    h[3] = use_gb;
+  }
+}
+
+// Global best <- iteration best when improved; source <- global best or
+// iteration best (routes and positions).
+__global__ void k_source(Colony C, Ants A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = C.n;
+  if (i >= n) return;
+  const DevState* st = C.st;
+  const int a = st->it_best_ant;
+  const int32_t r = A.route[(size_t)a * n + i];
+  const int32_t p = A.pos[(size_t)a * n + i];
+  if (st->gb_improved) {
+    C.gb_route[i] = r;
+    C.gb_pos[i] = p;
+  }
+  if (st->use_gb) {
+    C.src_route[i] = C.gb_route[i];
+    C.src_pos[i] = C.gb_pos[i];
+  } else {
+    C.src_route[i] = r;
+    C.src_pos[i] = p;
+  }
+}
+
+__global__ void k_state_init(Colony C, const int64_t* len) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevState* st = C.st;
+  const int64_t L = *len;
+  st->iter = 0;
+  st->init_len = L;
+  st->gb_len = L;
+  st->src_len = L;
+  st->it_best_len = L;
+  st->it_best_ant = 0;
+  st->use_gb = 1;
+  st->gb_improved = 0;
+  st->error = 0;
+  set_limits(C, st, L);
+  st->delta = __double2float_rn(1.0 / (double)L);
+}
+
+__global__ void k_positions(const int32_t* route, int32_t* pos, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) pos[route[i]] = i;
+}
+
+__global__ void k_tour_length(const int2* xy, const int32_t* route, int n, unsigned long long* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t d = 0;
+  if (i < n) d = euc2d(xy[route[i]], xy[route[i + 1 == n ? 0 : i + 1]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += shfl64_xor(d, o);
+  if ((threadIdx.x & 31) == 0 && d) atomicAdd(out, (unsigned long long)d);
+}
+
+}  // namespace
+
+cudaError_t launch_rows(const Colony& C, int update, cudaStream_t s) {
+  k_rows<<<(C.n + 255) / 256, 256, 0, s>>>(C, update);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_P(const Colony& C, cudaStream_t s) {
+  k_scan_P<<<1, 1024, 0, s>>>(C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best(const Colony& C, const Ants& A, cudaStream_t s) {
+  k_best<<<1, 1024, 0, s>>>(C, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source(const Colony& C, const Ants& A, cudaStream_t s) {
+  k_source<<<(C.n + 255) / 256, 256, 0, s>>>(C, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_init(const Colony& C, const int64_t* len, cudaStream_t s) {
+  k_state_init<<<1, 32, 0, s>>>(C, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_positions(const int32_t* route, int32_t* pos, int n, cudaStream_t s) {
+  k_positions<<<(n + 255) / 256, 256, 0, s>>>(route, pos, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tour_length(const int2* xy, const int32_t* route, int n, int64_t* out,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return e;
+  k_tour_length<<<(n + 255) / 256, 256, 0, s>>>(xy, route, n, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace faco

@@ -1,0 +1,221 @@
+// common.cuh -- device helpers and shared structures of the GB300 FACO library.
+//
+// Independent of the CPU oracle: nothing here is shared with it.  The
+// arithmetic follows the paper (Sec. 2.1 costs, Eq. 1 weights, Eq. 2 update)
+// and the readings documented in the library header.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace faco {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxK = 32;        // candidate list length supported (Sec. 4.1: 16)
+constexpr int kMaxKnn = 160;     // k + backup length supported by the list builder
+
+// Device error flags (bitwise or into DevState::error).
+enum : int32_t {
+  kErrCapacity = 1,
+  kErrTimeout = 2,
+  kErrInternal = 4,
+};
+
+// Per-ant counters (row of Ants::stats).
+enum : int {
+  kStAco = 0, kStNew, kStBackup, kStGlobal, kStCheck, kStPops, kStMoves2, kStMovesOr,
+  kStFlip, kStVerify, kNStats = 16
+};
+
+// Colony scalars that change on the device (read by graph-replayed kernels).
+struct DevState {
+  int64_t iter;          // iterations completed
+  int64_t gb_len;        // global-best length
+  int64_t src_len;       // length of the current source solution
+  int64_t it_best_len;   // iteration-best length of the last iteration
+  int64_t init_len;
+  double tmax_d, tmin_d; // trail limits (Sec. 4.5)
+  float tmax, tmin;      // the same, stored in FP32
+  float delta;           // deposit amount for the current source
+  int32_t it_best_ant;
+  int32_t use_gb;        // the current source is the global best
+  int32_t gb_improved;   // the last iteration improved the global best
+  int32_t error;         // kErr* flags
+  int32_t pad;
+  int64_t* hist;         // per-iteration history, 4 int64 per row
+  int64_t hist_cap;      // rows available
+};
+
+// Device pointers and sizes of one colony (passed by value).
+struct Colony {
+  int32_t n, k, bl, kw;  // kw = roulette width: 16 if k <= 16, else 32
+  uint64_t seed;
+  float rho;
+  int32_t min_new_edges;
+  int32_t oropt, verify;
+  double c_min;          // tau_min / tau_max ratio
+  double p_src_gb;
+  const int2* xy;        // [n] coordinates, node order
+  const int32_t* cand;   // [n][k] candidate lists
+  const int32_t* backup; // [n][bl] backup lists
+  const float* eta;      // [n][k] 1/d
+  float* tau;            // [n][k] pheromone on candidate edges
+  int32_t* src_route;    // [n] source solution
+  int32_t* src_pos;      // [n] its inverse
+  int32_t* gb_route;     // [n] global best
+  int32_t* gb_pos;       // [n]
+  float* Wsrc;           // [n][kw] tau*eta in source order, 0 beyond k
+  int32_t* Csrc;         // [n][kw] source position of each candidate, -1 beyond k
+  int2* XYsrc;           // [n] coordinates in source order
+  int32_t* Dsrc;         // [n] length of source edge (p, p+1)
+  int64_t* Psrc;         // [n+1] exclusive prefix sums of Dsrc
+  DevState* st;
+};
+
+// Per-ant buffers of one ant count.
+struct Ants {
+  int32_t m;             // ants per iteration
+  int32_t* route;        // [m][n]
+  int32_t* pos;          // [m][n]
+  int32_t* chk;          // [m][n] checklist (node ids)
+  int64_t* len;          // [m]
+  int64_t* stats;        // [m][kNStats]
+  int32_t* queue;        // [m][n] local-search FIFO
+  uint8_t* flags;        // [m][n] bit0 queued, bit1 popped this round (kept zero between uses)
+  int32_t* logb;         // [m][n] nodes popped this round, first pop order
+  uint32_t* vis_g;       // [m][words] visited bits when they do not fit shared memory
+  int32_t smem_vis;      // 1: visited bits live in shared memory
+  int32_t* pre_route;    // [m][n] optional: tours before local search
+  int64_t* pre_len;      // [m]
+  int32_t* pre_chk;      // [m][n]
+  int32_t* pre_nchk;     // [m]
+};
+
+// ---------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its definition:
+// ten rounds of two 32x32->64 multiplies with the Weyl key schedule.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Draw `idx` of stream (ant, iter, tag): word idx%4 of counter (idx/4, ant, iter, tag).
+__device__ __forceinline__ uint32_t draw(uint64_t seed, uint32_t idx, uint32_t ant, uint32_t iter,
+                                         uint32_t tag) {
+  const uint4 o = philox4x32_10(make_uint4(idx >> 2, ant, iter, tag), (uint32_t)seed,
+                                (uint32_t)(seed >> 32));
+  const uint32_t w = idx & 3u;
+  return w == 0 ? o.x : (w == 1 ? o.y : (w == 2 ? o.z : o.w));
+}
+
+// Top 24 bits times 2^-24: exact, in [0, 1).
+__device__ __forceinline__ float u01(uint32_t x) {
+  return __uint2float_rn(x >> 8) * (1.0f / 16777216.0f);
+}
+
+// ---------------------------------------------------------------------
+// EUC_2D: nint(sqrt(dx^2 + dy^2)) for coordinates in [0, 2^24).  The FP32
+// square root is only an estimate (off by at most 2); integer corrections
+// make r = floor(sqrt(m)) exactly, and sqrt(m) >= r + 1/2 <=> m - r^2 > r.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sqdist(int2 a, int2 b) {
+  const int64_t dx = (int64_t)a.x - b.x, dy = (int64_t)a.y - b.y;
+  return (uint64_t)(dx * dx + dy * dy);
+}
+
+__device__ __forceinline__ int32_t euc2d_m(uint64_t m) {
+  uint64_t r = (uint64_t)__fsqrt_rn(__ull2float_rn(m));
+  while (r * r > m) --r;
+  while ((r + 1) * (r + 1) <= m) ++r;
+  return (int32_t)(r + ((m - r * r) > r ? 1u : 0u));
+}
+
+__device__ __forceinline__ int32_t euc2d(int2 a, int2 b) { return euc2d_m(sqdist(a, b)); }
+
+// ---------------------------------------------------------------------
+// Roulette of Eq. 1 over W slots (weights tau*eta, zero when visited or
+// padding): inclusive Kogge-Stone scan (level `off` adds the value `off`
+// slots to the left), r = u * total, the first slot with positive weight
+// whose prefix exceeds r, else the last slot with positive weight.
+// ---------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ int roulette(const float (&w)[W], float u) {
+  float s[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) s[i] = w[i];
+#pragma unroll
+  for (int off = 1; off < W; off <<= 1) {
+#pragma unroll
+    for (int i = W - 1; i >= off; --i) s[i] = __fadd_rn(s[i - off], s[i]);
+  }
+  const float r = __fmul_rn(u, s[W - 1]);
+  int pick = -1;
+#pragma unroll
+  for (int i = W - 1; i >= 0; --i)
+    if (w[i] > 0.0f && s[i] > r) pick = i;
+  if (pick < 0) {
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (w[i] > 0.0f) pick = i;
+  }
+  return pick;
+}
+
+// ---------------------------------------------------------------------
+// Small warp helpers.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
+  return (int64_t)__shfl_sync(kFull, (unsigned long long)v, src);
+}
+
+__device__ __forceinline__ int64_t shfl64_xor(int64_t v, int o) {
+  return (int64_t)__shfl_xor_sync(kFull, (unsigned long long)v, o);
+}
+
+__device__ __forceinline__ int64_t shfl64_up(int64_t v, int o) {
+  return (int64_t)__shfl_up_sync(kFull, (unsigned long long)v, o);
+}
+
+// Lexicographic minimum of (key, idx) over the warp; every lane gets it.
+__device__ __forceinline__ void warp_min_key(uint64_t& key, int32_t& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t k2 = __shfl_xor_sync(kFull, (unsigned long long)key, o);
+    const int32_t i2 = __shfl_xor_sync(kFull, idx, o);
+    if (k2 < key || (k2 == key && i2 < idx)) {
+      key = k2;
+      idx = i2;
+    }
+  }
+}
+
+// Maximum gain, ties to the smallest order index; every lane gets it.
+__device__ __forceinline__ void warp_max_gain(int64_t& g, int32_t& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t g2 = shfl64_xor(g, o);
+    const int32_t i2 = __shfl_xor_sync(kFull, idx, o);
+    if (g2 > g || (g2 == g && i2 < idx)) {
+      g = g2;
+      idx = i2;
+    }
+  }
+}
+
+__device__ __forceinline__ int wrapn(int x, int n) {  // x in (-n, 2n)
+  return x < 0 ? x + n : (x >= n ? x - n : x);
+}
+
+}  // namespace faco

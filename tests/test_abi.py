@@ -1,0 +1,74 @@
+"""The C-ABI library without a GPU: it loads, exports every function that
+include/faco.h declares, and rejects invalid arguments before touching the
+device.  Without a GPU a valid call fails loudly (FACO_E_CUDA), never falls
+back to the CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2203_02228_gb300 import _lib, build, faco_params, params_default
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "faco.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(faco_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "faco_create" in names and "faco_iterate" in names and "faco_best" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_params_struct_matches_defaults(lib):
+    p = params_default()
+    assert p.seed == 1 and p.rho == np.float32(0.5) and p.min_new_edges == 8 and p.bl_size == 64
+    assert p.p_best == 0.05 and p.p_source_gb == 0.01 and p.oropt == 1 and p.verify_pass == 1
+    assert ctypes.sizeof(faco_params) == 64
+
+
+def test_invalid_arguments_are_rejected(lib):
+    xy = np.zeros((10, 2), np.int32)
+    xy[:, 0] = np.arange(10)
+    h = ctypes.c_void_p()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    assert lib.faco_create(P(xy), 2, 16, ctypes.byref(h)) == _lib.FACO_E_ARG  # n < 3
+    assert lib.faco_create(P(xy), 10, 1, ctypes.byref(h)) == _lib.FACO_E_ARG  # k < 2
+    assert lib.faco_create(P(xy), 10, 33, ctypes.byref(h)) == _lib.FACO_E_ARG  # k > 32
+    assert lib.faco_create(None, 10, 16, ctypes.byref(h)) == _lib.FACO_E_ARG
+    bad = xy.copy()
+    bad[3, 1] = 1 << 24
+    assert lib.faco_create(P(bad), 10, 16, ctypes.byref(h)) == _lib.FACO_E_ARG
+    bad[3, 1] = -1
+    assert lib.faco_create(P(bad), 10, 16, ctypes.byref(h)) == _lib.FACO_E_ARG
+    for field, val in (("rho", 1.0), ("rho", 0.0), ("p_best", 1.0), ("min_new_edges", 0),
+                       ("bl_size", -1), ("bl_size", 129), ("p_source_gb", 1.5)):
+        p = params_default(**{field: val})
+        assert lib.faco_create_ex(P(xy), 10, 16, ctypes.byref(p), ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_iterate(None, 4, 1) == _lib.FACO_E_ARG
+    assert lib.faco_best(None, None, 0, None) == _lib.FACO_E_ARG
+    assert lib.faco_strerror(_lib.FACO_E_CAPACITY).decode() == "device capacity exceeded"
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    xy = np.stack([np.arange(50), np.arange(50) * 3 % 17], 1).astype(np.int32)
+    h = ctypes.c_void_p()
+    rc = lib.faco_create(xy.ctypes.data_as(ctypes.c_void_p), 50, 16, ctypes.byref(h))
+    assert rc == _lib.FACO_E_CUDA
