@@ -26,7 +26,7 @@
 //   checklist    the head v of every new edge, in order.
 #include "common.cuh"
 #include "launch.h"
-#include "ls_array.cuh"
+#include "ls.cuh"
 
 namespace faco {
 
@@ -191,11 +191,17 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
       return __shfl_sync(kFull, q, __ffs(bal) - 1);
     }
   }
+  // global nearest unvisited node: scan visited words, skip full ones
   const int2 xu = C.XYsrc[pc];
   uint64_t bk = ~0ull;
   int32_t bi = INT_MAX;
-  for (int q = lane; q < n; q += 32) {
-    if (!vis_get(vis, q)) {
+  const int words = (n + 31) >> 5;
+  for (int wi = lane; wi < words; wi += 32) {
+    uint32_t fr = ~vis[wi];
+    if (wi == words - 1 && (n & 31)) fr &= (1u << (n & 31)) - 1u;
+    while (fr) {
+      const int q = wi * 32 + __ffs(fr) - 1;
+      fr &= fr - 1;
       const uint64_t m = sqdist(xu, C.XYsrc[q]);
       const int32_t node = C.src_route[q];
       if (m < bk || (m == bk && node < bi)) {
@@ -372,14 +378,11 @@ __global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
     }
   }
   // local search seeded with the checklist
-  LsEnv E;
-  E.n = n; E.k = C.k; E.oropt = C.oropt; E.verify = C.verify; E.xy = C.xy; E.cand = C.cand;
-  E.queue = A.queue + (size_t)ant * n;
-  E.flags = A.flags + (size_t)ant * n;
-  E.logb = A.logb + (size_t)ant * n;
-  ArrTour T{n, route, pos};
+  LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
+          A.logb + (size_t)ant * n};
+  ArrTour T{n, C.k, route, pos, C.xy, C.cand};
   LsStats S{0, 0, 0, 0, 0};
-  const int64_t gain = ls_array_run(E, T, chk, W.nchk, S);
+  const int64_t gain = ls_run(E, T, chk, W.nchk, S);
   if (lane == 0) {
     A.len[ant] = pre_len - gain;
     int64_t* st = A.stats + (size_t)ant * kNStats;

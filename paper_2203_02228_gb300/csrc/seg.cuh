@@ -1,0 +1,355 @@
+// seg.cuh -- an ant's tour held as runs of the source solution.
+//
+// After focused construction (Alg 2) an ant's tour is a concatenation of a
+// few runs of the source solution; the local search (Alg 3) then changes
+// the tour by reversals.  Instead of materialising route[]/pos[] arrays of
+// n entries per ant, a warp keeps the tour as a table of segments in shared
+// memory: segment id covers source positions [lo, lo+len) and ant positions
+// [off, off+len), traversed upwards (rev = 0) or downwards (rev = 1) in the
+// source.  Nodes are named by their source position.  Two orders index the
+// table: A (ids by ant position, A[0] at position 0) and B (ids by lo).
+// Segments never straddle ant position 0 nor the source's end, so every
+// lookup is a binary search.  A reversal of ant positions i..j splits the
+// segments at i and j+1, reverses that part of A and flips each segment's
+// direction -- exactly the array reversal, entry for entry, in O(segments).
+// Neighbouring segments that continue each other are merged back.  When the
+// table is full the operation reports failure and the caller redoes the ant
+// with explicit arrays (same result, more memory traffic).
+#pragma once
+
+#include "common.cuh"
+#include "ls.cuh"
+
+namespace faco {
+
+struct Seg {
+  int32_t lo, len, off, rev;
+};
+
+// Shared-memory table of one warp.
+struct SegTab {
+  Seg* sg;           // [cap] segments by id (ids 0..S-1)
+  uint16_t* A;       // [cap] ids in ant order
+  uint16_t* B;       // [cap] ids in source order
+  int32_t* offA;     // [cap] sg[A[r]].off
+  int32_t* loB;      // [cap] sg[B[r]].lo
+  uint16_t* tmp;     // [cap] scratch
+  int32_t* S;        // segment count (shared)
+  int cap;
+};
+
+// bytes of shared memory per warp for a table of `cap` segments
+__host__ __device__ constexpr size_t segtab_bytes(int cap) {
+  return (size_t)cap * (sizeof(Seg) + 3 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 16;
+}
+
+__device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
+  SegTab T;
+  T.sg = reinterpret_cast<Seg*>(base);
+  char* p = base + (size_t)cap * sizeof(Seg);
+  T.offA = reinterpret_cast<int32_t*>(p);
+  p += (size_t)cap * sizeof(int32_t);
+  T.loB = reinterpret_cast<int32_t*>(p);
+  p += (size_t)cap * sizeof(int32_t);
+  T.A = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * sizeof(uint16_t);
+  T.B = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * sizeof(uint16_t);
+  T.tmp = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * sizeof(uint16_t);
+  T.S = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+  T.cap = cap;
+  return T;
+}
+
+// Largest r in [0, S) with key[r] <= v (key ascending, key[0] <= v).
+__device__ __forceinline__ int bsearch_le(const int32_t* key, int S, int v) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (key[mid] <= v)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Insert val at index r of arr[0..S) (warp-collective).
+__device__ __forceinline__ void u16_insert(uint16_t* arr, int S, int r, uint16_t val) {
+  const int lane = lane_id();
+  for (int e = S - 1; e >= r; e -= 32) {
+    const int idx = e - lane;
+    uint16_t v = 0;
+    if (idx >= r) v = arr[idx];
+    __syncwarp();
+    if (idx >= r) arr[idx + 1] = v;
+    __syncwarp();
+  }
+  if (lane == 0) arr[r] = val;
+  __syncwarp();
+}
+
+// Remove index r of arr[0..S) (warp-collective).
+__device__ __forceinline__ void u16_remove(uint16_t* arr, int S, int r) {
+  const int lane = lane_id();
+  for (int e = r + 1; e < S; e += 32) {
+    const int idx = e + lane;
+    uint16_t v = 0;
+    if (idx < S) v = arr[idx];
+    __syncwarp();
+    if (idx < S) arr[idx - 1] = v;
+    __syncwarp();
+  }
+}
+
+// Rebuild the search keys from the orders (warp-collective).
+__device__ __forceinline__ void segtab_keys(const SegTab& T) {
+  const int S = *T.S;
+  for (int r = lane_id(); r < S; r += 32) {
+    T.offA[r] = T.sg[T.A[r]].off;
+    T.loB[r] = T.sg[T.B[r]].lo;
+  }
+  __syncwarp();
+}
+
+// Rank in B of segment id (by its lo).
+__device__ __forceinline__ int rank_B(const SegTab& T, int id) {
+  return bsearch_le(T.loB, *T.S, T.sg[id].lo);
+}
+
+// Ensure a segment starts at ant position t (0 < t < n).  Keys must be
+// current on entry and are current on exit.  false: table full.
+__device__ __noinline__ bool seg_split(const SegTab& T, int t) {
+  const int S = *T.S;
+  const int r = bsearch_le(T.offA, S, t);
+  const int id = T.A[r];
+  const Seg s = T.sg[id];
+  if (s.off == t) return true;
+  if (S >= T.cap) return false;
+  const int d = t - s.off;
+  const int nid = S;
+  const int rb = rank_B(T, id);
+  __syncwarp();
+  if (lane_id() == 0) {
+    if (!s.rev) {
+      T.sg[nid] = Seg{s.lo + d, s.len - d, t, 0};
+      T.sg[id].len = d;
+    } else {
+      T.sg[nid] = Seg{s.lo, s.len - d, t, 1};
+      T.sg[id].lo = s.lo + s.len - d;
+      T.sg[id].len = d;
+    }
+  }
+  __syncwarp();
+  u16_insert(T.A, S, r + 1, (uint16_t)nid);
+  u16_insert(T.B, S, s.rev ? rb : rb + 1, (uint16_t)nid);
+  if (lane_id() == 0) *T.S = S + 1;
+  __syncwarp();
+  segtab_keys(T);
+  return true;
+}
+
+// Drop id `dead` (already unlinked from A and B): move the last id into
+// its slot.  Orders must be consistent; keys are rebuilt by the caller.
+__device__ __forceinline__ void seg_free_id(const SegTab& T, int dead, int S_after) {
+  const int last = S_after;  // id numbers 0..S_after are in use before the move
+  if (dead == last) return;
+  const int lane = lane_id();
+  // re-point the references to `last`
+  for (int r = lane; r < S_after; r += 32) {
+    if (T.A[r] == last) T.A[r] = (uint16_t)dead;
+    if (T.B[r] == last) T.B[r] = (uint16_t)dead;
+  }
+  __syncwarp();
+  if (lane == 0) T.sg[dead] = T.sg[last];
+  __syncwarp();
+}
+
+// Merge ant-adjacent segments that continue each other in the source
+// (never across ant position 0).  Keys are rebuilt.
+__device__ __noinline__ void seg_merge_all(const SegTab& T) {
+  const int lane = lane_id();
+  for (;;) {
+    const int S = *T.S;
+    int found = -1;
+    for (int r0 = 0; r0 + 1 < S && found < 0; r0 += 32) {
+      const int r = r0 + lane;
+      bool m = false;
+      if (r + 1 < S) {
+        const Seg a = T.sg[T.A[r]], b = T.sg[T.A[r + 1]];
+        m = a.rev == b.rev && (a.rev ? (b.lo + b.len == a.lo) : (a.lo + a.len == b.lo));
+      }
+      const unsigned bal = __ballot_sync(kFull, m);
+      if (bal) found = r0 + __ffs(bal) - 1;
+    }
+    if (found < 0) break;
+    const int ia = T.A[found], ib = T.A[found + 1];
+    const Seg a = T.sg[ia], b = T.sg[ib];
+    const int rbb = rank_B(T, ib);
+    __syncwarp();
+    if (lane == 0) {
+      T.sg[ia].len = a.len + b.len;
+      if (a.rev) T.sg[ia].lo = b.lo;
+    }
+    __syncwarp();
+    u16_remove(T.A, S, found + 1);
+    u16_remove(T.B, S, rbb);
+    seg_free_id(T, ib, S - 1);
+    if (lane == 0) *T.S = S - 1;
+    __syncwarp();
+    segtab_keys(T);
+  }
+}
+
+// Tour over the segment table (nodes = source positions).
+struct SegTour {
+  int n, k, kw;
+  SegTab T;
+  const int2* xy;       // coordinates by source position
+  const int32_t* cn;    // candidate source positions by source position [n][kw]
+
+  __device__ __forceinline__ int pos_of(int q) const {
+    const int r = bsearch_le(T.loB, *T.S, q);
+    const Seg s = T.sg[T.B[r]];
+    return s.off + (s.rev ? s.lo + s.len - 1 - q : q - s.lo);
+  }
+  __device__ __forceinline__ int at(int t) const {
+    const int r = bsearch_le(T.offA, *T.S, t);
+    const Seg s = T.sg[T.A[r]];
+    const int d = t - s.off;
+    return s.rev ? s.lo + s.len - 1 - d : s.lo + d;
+  }
+  __device__ __forceinline__ int2 coord(int q) const { return xy[q]; }
+  __device__ __forceinline__ int cand(int q, int s) const { return cn[(size_t)q * kw + s]; }
+
+  // Reverse the forward span x..y, or its complement when longer than n/2
+  // (the array rule, entry for entry).  false: the table is full.
+  __device__ __noinline__ bool flip(int x, int y, LsStats& St) {
+    const int lane = lane_id();
+    int i = pos_of(x), j = pos_of(y);
+    int L = j - i;
+    if (L < 0) L += n;
+    L += 1;
+    if (2 * L > n) {
+      const int i2 = (j + 1 == n) ? 0 : j + 1;
+      const int j2 = (i == 0) ? n - 1 : i - 1;
+      i = i2;
+      j = j2;
+      L = n - L;
+    }
+    St.flip += L;
+    if (L <= 1) return true;
+    const int j1 = (j + 1 == n) ? 0 : j + 1;
+    if (i != 0 && !seg_split(T, i)) return false;
+    if (j1 != 0 && !seg_split(T, j1)) return false;
+    const int S = *T.S;
+    const int ri = bsearch_le(T.offA, S, i);
+    const int rj = (j1 == 0) ? S - 1 : bsearch_le(T.offA, S, j1) - 1;
+    if (i <= j) {
+      // contiguous ranks ri..rj: new off = i + j + 1 - off - len, direction flips
+      const int c = rj - ri + 1;
+      for (int m = lane; m < c; m += 32) {
+        Seg& s = T.sg[T.A[ri + m]];
+        s.off = i + j + 1 - s.off - s.len;
+        s.rev ^= 1;
+      }
+      __syncwarp();
+      for (int m = lane; m < c / 2; m += 32) {
+        const uint16_t a = T.A[ri + m], b = T.A[rj - m];
+        T.A[ri + m] = b;
+        T.A[rj - m] = a;
+      }
+      __syncwarp();
+      segtab_keys(T);
+    } else {
+      // the span wraps: ranks ri..S-1 then 0..rj; lay the reversed list
+      // out from position i, cutting the segment that crosses position 0
+      const int clo = rj + 1, chi = S - ri, c = clo + chi;
+      // R[m] = A[rj - m] (m < clo), A[S - 1 - (m - clo)] (m >= clo)
+      for (int m = lane; m < c; m += 32) T.tmp[m] = m < clo ? T.A[rj - m] : T.A[S - 1 - (m - clo)];
+      __syncwarp();
+      // new offsets by a sequential prefix over R (lane 0; c is small)
+      int straddle = -1, cut = 0;
+      if (lane == 0) {
+        int pos = i;
+        for (int m = 0; m < c; ++m) {
+          Seg& s = T.sg[T.tmp[m]];
+          s.rev ^= 1;
+          s.off = pos;
+          if (pos < n && pos + s.len > n) {
+            straddle = m;
+            cut = n - pos;
+          }
+          pos += s.len;
+          if (pos >= n && s.off >= n) s.off -= n;
+        }
+        for (int m = 0; m < c; ++m) {
+          Seg& s = T.sg[T.tmp[m]];
+          if (s.off >= n) s.off -= n;
+        }
+      }
+      straddle = __shfl_sync(kFull, straddle, 0);
+      cut = __shfl_sync(kFull, cut, 0);
+      __syncwarp();
+      int S2 = S;
+      int nid = -1;
+      if (straddle >= 0) {
+        if (S >= T.cap) return false;
+        const int id = T.tmp[straddle];
+        const Seg s = T.sg[id];
+        nid = S;
+        const int rb = bsearch_le(T.loB, S, s.lo);
+        __syncwarp();
+        if (lane == 0) {
+          // id keeps ant positions [s.off, n); nid takes [0, s.len - cut)
+          if (!s.rev) {
+            T.sg[nid] = Seg{s.lo + cut, s.len - cut, 0, 0};
+            T.sg[id].len = cut;
+          } else {
+            T.sg[nid] = Seg{s.lo, s.len - cut, 0, 1};
+            T.sg[id].lo = s.lo + s.len - cut;
+            T.sg[id].len = cut;
+          }
+        }
+        __syncwarp();
+        u16_insert(T.B, S, s.rev ? rb : rb + 1, (uint16_t)nid);
+        S2 = S + 1;
+      }
+      // new A: [nid] + wrapped part of R + middle A[clo..ri) + unwrapped part of R
+      // R is ordered by new position: the unwrapped part (offsets >= i) comes
+      // first in R, the wrapped part after it.
+      int nhi = 0;  // R entries placed in [i, n): up to and including the straddler
+      if (lane == 0) {
+        int pos = i;
+        nhi = 0;
+        for (int m = 0; m < c; ++m) {
+          if (pos >= n) break;
+          pos += T.sg[T.tmp[m]].len;
+          ++nhi;
+        }
+        if (straddle >= 0) nhi = straddle + 1;
+      }
+      nhi = __shfl_sync(kFull, nhi, 0);
+      // assemble into the tail of tmp: tmp[c..c+S2)
+      uint16_t* out = T.tmp + c;
+      const int mid = ri - clo;
+      const int head = (nid >= 0) ? 1 : 0;
+      const int nlo = c - nhi;
+      if (lane == 0 && nid >= 0) out[0] = (uint16_t)nid;
+      for (int m = lane; m < nlo; m += 32) out[head + m] = T.tmp[nhi + m];
+      for (int m = lane; m < mid; m += 32) out[head + nlo + m] = T.A[clo + m];
+      for (int m = lane; m < nhi; m += 32) out[head + nlo + mid + m] = T.tmp[m];
+      __syncwarp();
+      for (int m = lane; m < S2; m += 32) T.A[m] = out[m];
+      __syncwarp();
+      if (lane == 0) *T.S = S2;
+      __syncwarp();
+      segtab_keys(T);
+    }
+    seg_merge_all(T);
+    return true;
+  }
+};
+
+}  // namespace faco

@@ -10,7 +10,7 @@
 
 #include "common.cuh"
 #include "launch.h"
-#include "ls_array.cuh"
+#include "ls.cuh"
 
 namespace faco {
 
@@ -47,11 +47,16 @@ __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int
       if (bal) v = __shfl_sync(kFull, c, __ffs(bal) - 1);
     }
     if (v < 0) {
+      // global nearest unvisited node: scan visited words, skip full ones
       const int2 xu = xy[u];
       uint64_t bk = ~0ull;
       int32_t bi = INT_MAX;
-      for (int w = lane; w < n; w += 32) {
-        if (!((vis[w >> 5] >> (w & 31)) & 1u)) {
+      for (int wi = lane; wi < words; wi += 32) {
+        uint32_t fr = ~vis[wi];
+        if (wi == words - 1 && (n & 31)) fr &= (1u << (n & 31)) - 1u;
+        while (fr) {
+          const int w = wi * 32 + __ffs(fr) - 1;
+          fr &= fr - 1;
           const uint64_t m = sqdist(xu, xy[w]);
           if (m < bk || (m == bk && w < bi)) {
             bk = m;
@@ -71,15 +76,162 @@ __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int
   }
 }
 
-__global__ void __launch_bounds__(32) k_init_ls(const int2* xy, int n, const int32_t* cand, int k,
-                                                int oropt, int verify, int32_t* route, int32_t* pos,
-                                                int32_t* queue, uint8_t* flags, int32_t* logb) {
-  LsEnv E;
-  E.n = n; E.k = k; E.oropt = oropt; E.verify = verify; E.xy = xy; E.cand = cand;
-  E.queue = queue; E.flags = flags; E.logb = logb;
-  ArrTour T{n, route, pos};
-  LsStats S{0, 0, 0, 0, 0};
-  ls_array_run(E, T, route, n, S);
+// Reverse the forward span x..y (or its complement) with the whole block.
+__device__ void cta_flip(ArrTour& T, int x, int y) {
+  const int n = T.n;
+  __syncthreads();
+  int i = T.pos[x], j = T.pos[y];
+  __syncthreads();  // every thread has read i, j before any position moves
+  int L = j - i;
+  if (L < 0) L += n;
+  L += 1;
+  if (2 * L > n) {
+    const int i2 = (j + 1 == n) ? 0 : j + 1;
+    const int j2 = (i == 0) ? n - 1 : i - 1;
+    i = i2;
+    j = j2;
+    L = n - L;
+  }
+  const int half = L >> 1;
+  for (int t = threadIdx.x; t < half; t += blockDim.x) {
+    int ia = i + t;
+    if (ia >= n) ia -= n;
+    int ib = j - t;
+    if (ib < 0) ib += n;
+    const int va = T.route[ia], vb = T.route[ib];
+    T.route[ia] = vb;
+    T.route[ib] = va;
+    T.pos[vb] = ia;
+    T.pos[va] = ib;
+  }
+  __syncthreads();
+}
+
+__device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4) {
+  const bool fwd = tour_succ(T, n1) == n2;
+  if (fwd)
+    cta_flip(T, n2, n3);
+  else
+    cta_flip(T, n1, n4);
+}
+
+// The local search of ls_array.cuh with every node queued (the initial
+// tour), run by one block of 32 warps.  Each round, warp w evaluates the
+// w-th queued node on the current tour; the entries are then popped in
+// queue order up to and including the first one that found a move, which
+// is applied.  Nothing changes the tour between the confirmed evaluations,
+// so the result is exactly that of popping one node at a time.
+__global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand, int k,
+                                                  int oropt, int verify, int32_t* route, int32_t* pos,
+                                                  int32_t* queue, uint8_t* flags, int32_t* logb) {
+  __shared__ int64_t s_gain[32];
+  __shared__ int s_mv[32][8];
+  __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win;
+  LsEnv E{n, oropt, verify, queue, flags, logb};
+  ArrTour T{n, k, route, pos, xy, cand};
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const int x = route[i];
+    queue[i] = x;
+    flags[x] = 1;
+  }
+  if (tid == 0) {
+    s_qh = 0; s_qn = n; s_nlog = 0; s_changes = 0; s_moves_round = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const int qh = s_qh, qn = s_qn;
+    if (qn == 0 || s_changes >= n) {
+      if (s_changes >= n || !verify || s_moves_round == 0) break;
+      const int nl = s_nlog;  // verify round: queue again the nodes popped
+      for (int i = tid; i < nl; i += blockDim.x) {
+        const int x = logb[i];
+        queue[i] = x;
+        flags[x] = 1;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        s_qh = 0; s_qn = nl; s_nlog = 0; s_moves_round = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const int W = qn < 32 ? qn : 32;
+    if (w < W) {
+      int idx = qh + w;
+      if (idx >= n) idx -= n;
+      const int a = queue[idx];
+      int mv[7];
+      int64_t g = eval_2opt(T, a, mv);
+      int type = 0;
+      if (!(g > 0) && oropt) {
+        g = eval_or(T, a, mv);
+        type = 1;
+      }
+      if (lane == 0) {
+        s_gain[w] = g > 0 ? g : 0;
+        for (int t = 0; t < 7; ++t) s_mv[w][t] = mv[t];
+        s_mv[w][7] = type;
+      }
+    }
+    __syncthreads();
+    if (w == 0) {
+      const unsigned bal = __ballot_sync(kFull, lane < W && s_gain[lane] > 0);
+      const int first = bal ? __ffs(bal) - 1 : W;
+      const int cnt = bal ? first + 1 : W;  // queue entries popped this round
+      int a = -1;
+      bool first_pop = false;
+      if (lane < cnt) {
+        int idx = qh + lane;
+        if (idx >= n) idx -= n;
+        a = queue[idx];
+        const uint8_t f = flags[a];
+        first_pop = !(f & 2);
+        flags[a] = (uint8_t)((f & ~1) | 2);
+      }
+      const unsigned fb = __ballot_sync(kFull, first_pop);
+      if (first_pop) logb[s_nlog + __popc(fb & ((1u << lane) - 1u))] = a;
+      __syncwarp();
+      if (lane == 0) {
+        s_nlog += __popc(fb);
+        int h = qh + cnt;
+        if (h >= n) h -= n;
+        s_qh = h;
+        s_qn = qn - cnt;
+        s_win = bal ? first : -1;
+      }
+    }
+    __syncthreads();
+    const int win = s_win;
+    if (win >= 0) {
+      int mv[8];
+      for (int t = 0; t < 8; ++t) mv[t] = s_mv[win][t];
+      if (mv[7] == 0) {
+        cta_flip(T, mv[1], mv[2]);
+      } else {
+        cta_move2(T, mv[0], mv[1], mv[4], mv[5]);
+        cta_move2(T, mv[0], mv[4], mv[3], mv[2]);
+        if (mv[6]) cta_move2(T, mv[4], mv[2], mv[1], mv[5]);
+      }
+      if (tid == 0) {
+        int qn2 = s_qn;
+        const int np = mv[7] == 0 ? 4 : 6;
+        for (int t = 0; t < np; ++t) ls_push0(E, mv[t], s_qh, qn2);
+        s_qn = qn2;
+        s_changes++;
+        s_moves_round++;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  const int qh = s_qh, qn = s_qn, nl = s_nlog;
+  for (int t = tid; t < qn; t += blockDim.x) {
+    int i = qh + t;
+    if (i >= n) i -= n;
+    flags[queue[i]] = 0;
+  }
+  for (int i = tid; i < nl; i += blockDim.x) flags[logb[i]] = 0;
 }
 
 // what = 0: Philox draws   in: uint32 [count][4] = (idx, ant, iter, tag) -> out uint32
@@ -126,7 +278,7 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, int k, int oropt, int verify,
                            int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s) {
-  k_init_ls<<<1, 32, 0, s>>>(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
+  k_init_ls<<<1, 1024, 0, s>>>(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
   return cudaGetLastError();
 }
 
