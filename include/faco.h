@@ -61,6 +61,11 @@ typedef struct {
   int32_t verify_pass;    /* 1: re-queue popped nodes until a clean round (1)     */
   int32_t keep_ant_tours; /* 1: keep every ant's last tour for faco_get_ant_tours */
   int32_t keep_pre_ls;    /* 1: also keep tours before local search (tests)       */
+  int32_t seg_cap;        /* per-ant tour table in shared memory, in segments:   */
+                          /* -1 = sized from shared memory (default), 0 = every  */
+                          /* ant on explicit n-entry arrays, 8..4096 = that size */
+                          /* (an ant whose table fills up is redone on arrays;   */
+                          /* results are identical in every case)                */
   void* stream;           /* cudaStream_t to enqueue on (NULL = own stream)       */
 } faco_params;
 
@@ -84,6 +89,10 @@ typedef struct {
   int64_t moves_or;        /* applied Or-opt moves (sum)                   */
   int64_t flip_elems;      /* elements moved by reversals (sum)            */
   int64_t kernel_launches; /* kernels this context has launched so far     */
+  int64_t redone_ants;     /* ants whose segment table filled up and that  */
+                           /* were rebuilt on explicit arrays (sum)        */
+  int32_t seg_cap;         /* segments per ant table (0: arrays only)      */
+  int32_t pad;
 } faco_stats;
 
 /* Fills *p with the defaults listed above.  Errors: FACO_E_ARG if p is NULL. */
@@ -172,6 +181,11 @@ int faco_get_history(faco_ctx* c, int64_t* hist, int64_t max_iters, int64_t* row
 int faco_get_ant_tours(faco_ctx* c, int32_t* tours, int64_t* lens);
 int faco_get_ant_pre(faco_ctx* c, int32_t* tours, int64_t* lens, int32_t* checklists,
                      int32_t* nchecks);
+/* Per-ant counters (ants x 16 int64, accumulated over the iterations run
+ * with the current ant count): select_next_node calls, new edges, backup
+ * picks, global picks, checklist length, queue pops, 2-opt moves, Or-opt
+ * moves, reversed elements, verify rounds, redone on arrays, 0 x 5. */
+int faco_get_ant_stats(faco_ctx* c, int64_t* stats);
 
 /* ---- device self-test hook (used by the test-suite) ----------------------
  * Runs one of the library's device primitives on `count` inputs copied from

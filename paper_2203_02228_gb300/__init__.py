@@ -185,6 +185,12 @@ class Colony:
         _lib.check(self._L.faco_get_history(self._h, _ptr(h), m, ctypes.byref(rows)), "faco_get_history")
         return h[:rows.value]
 
+    def ant_stats(self) -> np.ndarray:
+        m = self.stats().ants
+        st = np.zeros((m, 16), np.int64)
+        _lib.check(self._L.faco_get_ant_stats(self._h, _ptr(st)), "faco_get_ant_stats")
+        return st
+
     def profile(self, on: bool = True) -> None:
         _lib.check(self._L.faco_profile_enable(self._h, int(on)), "faco_profile_enable")
 

@@ -37,6 +37,7 @@ class faco_params(ctypes.Structure):
         ("verify_pass", ctypes.c_int32),
         ("keep_ant_tours", ctypes.c_int32),
         ("keep_pre_ls", ctypes.c_int32),
+        ("seg_cap", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -60,6 +61,9 @@ class faco_stats(ctypes.Structure):
         ("moves_or", ctypes.c_int64),
         ("flip_elems", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
+        ("redone_ants", ctypes.c_int64),
+        ("seg_cap", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -106,7 +110,8 @@ def load():
             "faco_get_history": (ctypes.c_int, [vp, vp, i64, P(i64)]),
             "faco_get_ant_tours": (ctypes.c_int, [vp, vp, vp]),
             "faco_get_ant_pre": (ctypes.c_int, [vp, vp, vp, vp, vp]),
-            "faco_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "faco_get_ant_stats": (ctypes.c_int, [vp, vp]),
+            "faco_profile_enable":(ctypes.c_int, [vp, ctypes.c_int]),
             "faco_profile_read": (ctypes.c_int, [vp, P(ctypes.c_double), P(i64)]),
             "faco_test_device":(ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_size_t,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),

@@ -14,6 +14,12 @@
 // pick is the ant's next step.  The result equals the sequential walk step
 // for step.
 //
+// The tour is a sequence of runs of the source.  The main kernel keeps it
+// that way -- a segment table in shared memory (seg.cuh) on which the local
+// search runs -- so an ant never writes n-entry arrays.  If an ant's table
+// fills up, the ant is marked and redone by the array kernel, which writes
+// route[]/pos[] explicitly; both give the same tour.
+//
 // Readings (shared with the oracle, decided there independently):
 //   start node   floor(x * n / 2^32) of draw 0;
 //   roulette     Eq. 1 with alpha = beta = 1 (see common.cuh);
@@ -27,6 +33,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "ls.cuh"
+#include "seg.cuh"
 
 namespace faco {
 
@@ -147,11 +154,57 @@ struct Walk {
   int new_edges, nchk;
   int64_t len;     // length of the closed runs and connecting edges
   int64_t aco, backup, global;
+  int64_t fall_ns;  // time in global nearest-unvisited scans
+  bool segs;       // emit a segment table instead of route/pos arrays
+  bool overflow;   // the segment table is full
+  SegTab tab;
 };
+
+// Closes the current run: appends its segment(s) to the table.  The run
+// occupies ant positions [kf - run_len, kf).
+__device__ __forceinline__ void close_run(const Colony& C, Walk& W) {
+  if (!W.segs || W.overflow) return;
+  const int n = C.n, len = W.run_len, off = W.kf - len;
+  const int S = *W.tab.S;
+  if (S + 2 > W.tab.cap) {
+    W.overflow = true;
+    return;
+  }
+  if (lane_id() == 0) {
+    Seg* sg = W.tab.sg;
+    int add = 1;
+    if (W.dir >= 0) {
+      const int f = W.run_first;
+      if (f + len <= n) {
+        sg[S] = Seg{f, len, off, 0};
+      } else {
+        const int l1 = n - f;
+        sg[S] = Seg{f, l1, off, 0};
+        sg[S + 1] = Seg{0, len - l1, off + l1, 0};
+        add = 2;
+      }
+    } else {
+      const int f = W.run_first;
+      if (f - len + 1 >= 0) {
+        sg[S] = Seg{f - len + 1, len, off, 1};
+      } else {
+        const int l1 = f + 1;
+        sg[S] = Seg{0, l1, off, 1};
+        sg[S + 1] = Seg{n - (len - l1), len - l1, off + l1, 1};
+        add = 2;
+      }
+    }
+    W.tab.A[S] = (uint16_t)S;
+    if (add == 2) W.tab.A[S + 1] = (uint16_t)(S + 1);
+    *W.tab.S = S + add;
+  }
+  __syncwarp();
+}
 
 // Writes route/pos for the c positions following pc in direction dir.
 __device__ __forceinline__ void place_run(const Colony& C, int32_t* route, int32_t* pos, const Walk& W,
                                           int dir, int c) {
+  if (W.segs) return;
   const int n = C.n, lane = lane_id();
   constexpr int U = 8;
   for (int i0 = 0; i0 < c; i0 += 32 * U) {
@@ -192,6 +245,7 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
     }
   }
   // global nearest unvisited node: scan visited words, skip full ones
+  const uint64_t t0 = global_ns();
   const int2 xu = C.XYsrc[pc];
   uint64_t bk = ~0ull;
   int32_t bi = INT_MAX;
@@ -212,6 +266,7 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
   }
   warp_min_key(bk, bi);
   W.global++;
+  W.fall_ns += (int64_t)(global_ns() - t0);
   if (bi < 0 || bi >= n) {  // cannot happen while a node is unvisited
     if (lane == 0) atomicOr(&C.st->error, kErrInternal);
     return pc == 0 ? n - 1 : pc - 1;
@@ -223,12 +278,12 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
 __device__ __forceinline__ void place_step(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
                                            int32_t* chk, Walk& W, int q) {
   const int n = C.n, lane = lane_id();
-  const int node = C.src_route[q];
   const int up = W.pc + 1 == n ? 0 : W.pc + 1;
   const int dn = W.pc == 0 ? n - 1 : W.pc - 1;
-  if (q != up && q != dn) {  // new edge
+  if (q != up && q != dn) {  // new edge: the current run ends here
     W.len += run_sum(C, W.run_first, W.dir, W.run_len) + euc2d(C.XYsrc[W.pc], C.XYsrc[q]);
-    if (lane == 0) chk[W.nchk] = node;
+    close_run(C, W);
+    if (lane == 0) chk[W.nchk] = W.segs ? q : C.src_route[q];
     W.nchk++;
     W.new_edges++;
     W.run_first = q;
@@ -239,8 +294,11 @@ __device__ __forceinline__ void place_step(const Colony& C, int32_t* route, int3
     W.run_len++;
   }
   if (lane == 0) {
-    route[W.kf] = node;
-    pos[node] = W.kf;
+    if (!W.segs) {
+      const int node = C.src_route[q];
+      route[W.kf] = node;
+      pos[node] = W.kf;
+    }
     vis[q >> 5] |= 1u << (q & 31);
   }
   __syncwarp();
@@ -309,37 +367,29 @@ __device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32
   }
 }
 
+// Focused construction of one ant.  Returns the tour length.
 template <int KW>
-__global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
-  extern __shared__ uint32_t smem_vis[];
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
-  const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (ant >= A.m) return;
-  const int n = C.n;
+__device__ __forceinline__ int64_t construct(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
+                                             int32_t* chk, Walk& W, uint32_t ant, uint32_t iter) {
+  const int n = C.n, lane = lane_id();
   const int words = (n + 31) >> 5;
-  uint32_t* vis = A.smem_vis ? smem_vis + (size_t)wib * words : A.vis_g + (size_t)ant * words;
   for (int i = lane; i < words; i += 32) vis[i] = 0;
   __syncwarp();
-  const uint32_t iter = (uint32_t)(C.st->iter + 1);
-  int32_t* route = A.route + (size_t)ant * n;
-  int32_t* pos = A.pos + (size_t)ant * n;
-  int32_t* chk = A.chk + (size_t)ant * n;
-
-  Walk W;
-  {
-    const uint32_t x0 = draw(C.seed, 0, (uint32_t)ant, iter, 0);
-    const int s0 = (int)(((uint64_t)x0 * (uint64_t)n) >> 32);
-    const int q0 = C.src_pos[s0];
-    if (lane == 0) {
+  const uint32_t x0 = draw(C.seed, 0, ant, iter, 0);
+  const int s0 = (int)(((uint64_t)x0 * (uint64_t)n) >> 32);
+  const int q0 = C.src_pos[s0];
+  if (lane == 0) {
+    if (!W.segs) {
       route[0] = s0;
       pos[s0] = 0;
-      vis[q0 >> 5] |= 1u << (q0 & 31);
     }
-    __syncwarp();
-    W.kf = 1; W.pc = q0; W.dir = 0; W.run_first = q0; W.run_len = 1; W.first_q = q0;
-    W.new_edges = 0; W.nchk = 0; W.len = 0; W.aco = 0; W.backup = 0; W.global = 0;
+    vis[q0 >> 5] |= 1u << (q0 & 31);
   }
-  while (W.kf < n) {
+  __syncwarp();
+  W.kf = 1; W.pc = q0; W.dir = 0; W.run_first = q0; W.run_len = 1; W.first_q = q0;
+  W.new_edges = 0; W.nchk = 0; W.len = 0; W.aco = 0; W.backup = 0; W.global = 0;
+  W.overflow = false;
+  while (W.kf < n && !W.overflow) {
     if (W.new_edges >= C.min_new_edges) {
       // complete along the source: forward, then backward
       int c = unvisited_run(vis, n, W.pc + 1 == n ? 0 : W.pc + 1, 1);
@@ -361,17 +411,87 @@ __global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
         W.kf += c;
       }
       if (W.kf >= n) break;
-      aco_steps<KW>(C, route, pos, vis, chk, W, 1, (uint32_t)ant, iter);
+      aco_steps<KW>(C, route, pos, vis, chk, W, 1, ant, iter);
     } else {
-      aco_steps<KW>(C, route, pos, vis, chk, W, W.dir != 0 ? 32 : 1, (uint32_t)ant, iter);
+      aco_steps<KW>(C, route, pos, vis, chk, W, W.dir != 0 ? 32 : 1, ant, iter);
     }
   }
-  const int64_t pre_len = W.len + run_sum(C, W.run_first, W.dir, W.run_len) +
-                          euc2d(C.XYsrc[W.pc], C.XYsrc[W.first_q]);
+  const int64_t L = W.len + run_sum(C, W.run_first, W.dir, W.run_len) +
+                    euc2d(C.XYsrc[W.pc], C.XYsrc[W.first_q]);
+  close_run(C, W);
+  return L;
+}
+
+// Writes the table's tour as node ids (source order -> node ids).
+__device__ void seg_materialize(const Colony& C, const SegTab& T, int32_t* route) {
+  const int S = *T.S;
+  const int n = C.n;
+  for (int r = 0; r < S; ++r) {
+    const Seg s = T.sg[T.A[r]];
+    for (int d = lane_id(); d < s.len; d += 32) {
+      const int q = s.rev ? s.lo + s.len - 1 - d : s.lo + d;
+      const int t = s.off + d;
+      if ((unsigned)q < (unsigned)n && (unsigned)t < (unsigned)n) route[t] = C.src_route[q];
+    }
+  }
   __syncwarp();
+}
+
+// B = ids by lo (ranks by counting: lo values are distinct); keys.
+__device__ void seg_finish_construction(const SegTab& T) {
+  const int S = *T.S;
+  for (int id = lane_id(); id < S; id += 32) {
+    const int lo = T.sg[id].lo;
+    int r = 0;
+    for (int o = 0; o < S; ++o) r += T.sg[o].lo < lo;
+    T.B[r] = (uint16_t)id;
+  }
+  __syncwarp();
+  segtab_keys(T);
+}
+
+template <int KW, bool SEGS>
+__global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
+  extern __shared__ __align__(16) char smem[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (ant >= A.m) return;
+  if (!SEGS && A.redo && !A.redo[ant]) return;  // array kernel: only the ants the table could not hold
+  const int n = C.n;
+  const int words = (n + 31) >> 5;
+  const size_t vis_bytes = ((size_t)words * 4 + 15) & ~(size_t)15;
+  const size_t per_warp = SEGS ? vis_bytes + segtab_bytes(A.seg_cap) : (A.smem_vis ? vis_bytes : 0);
+  char* mine = smem + (size_t)wib * per_warp;
+  uint32_t* vis = (SEGS || A.smem_vis) ? reinterpret_cast<uint32_t*>(mine) : A.vis_g + (size_t)ant * words;
+  const uint32_t iter = (uint32_t)(C.st->iter + 1);
+  const uint64_t t_start = global_ns();
+  int32_t* route = A.route + (size_t)ant * n;
+  int32_t* pos = A.pos + (size_t)ant * n;
+  int32_t* chk = A.chk + (size_t)ant * n;
+
+  Walk W;
+  W.segs = SEGS;
+  if (SEGS) {
+    W.tab = segtab_at(mine + vis_bytes, A.seg_cap);
+    if (lane == 0) *W.tab.S = 0;
+    __syncwarp();
+  }
+  W.fall_ns = 0;
+  const int64_t pre_len = construct<KW>(C, route, pos, vis, chk, W, (uint32_t)ant, iter);
+  const uint64_t t_cons = global_ns();
+  if (SEGS && W.overflow) {
+    if (lane == 0) A.redo[ant] = 1;
+    return;
+  }
+  if (SEGS) seg_finish_construction(W.tab);
   if (A.pre_route) {
-    for (int i = lane; i < n; i += 32) A.pre_route[(size_t)ant * n + i] = route[i];
-    for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = chk[i];
+    if (SEGS) {
+      seg_materialize(C, W.tab, A.pre_route + (size_t)ant * n);
+      for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = C.src_route[chk[i]];
+    } else {
+      for (int i = lane; i < n; i += 32) A.pre_route[(size_t)ant * n + i] = route[i];
+      for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = chk[i];
+    }
     if (lane == 0) {
       A.pre_len[ant] = pre_len;
       A.pre_nchk[ant] = W.nchk;
@@ -380,38 +500,86 @@ __global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
   // local search seeded with the checklist
   LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
           A.logb + (size_t)ant * n};
-  ArrTour T{n, C.k, route, pos, C.xy, C.cand};
   LsStats S{0, 0, 0, 0, 0};
-  const int64_t gain = ls_run(E, T, chk, W.nchk, S);
+  int64_t gain;
+  if (SEGS) {
+    SegTour T{n, C.k, C.kw, W.tab, C.XYsrc, C.Csrc};
+    gain = ls_run(E, T, chk, W.nchk, S);
+    if (gain < 0) {  // the table filled up during the search
+      if (lane == 0) A.redo[ant] = 1;
+      return;
+    }
+    // hand the tour over: segments in ant order
+    const int Sn = *W.tab.S;
+    int4* out = A.segs + (size_t)ant * A.seg_cap;
+    for (int r = lane; r < Sn; r += 32) {
+      const Seg s = W.tab.sg[W.tab.A[r]];
+      out[r] = make_int4(s.lo, s.len, s.off, s.rev);
+    }
+    if (lane == 0) A.nseg[ant] = Sn;
+    if (A.keep_tours) seg_materialize(C, W.tab, route);
+  } else {
+    ArrTour T{n, C.k, route, pos, C.xy, C.cand};
+    gain = ls_run(E, T, chk, W.nchk, S);
+    if (lane == 0 && A.nseg) A.nseg[ant] = -1;  // tour is in route/pos
+  }
   if (lane == 0) {
     A.len[ant] = pre_len - gain;
+    if (A.redo) A.redo[ant] = 0;
     int64_t* st = A.stats + (size_t)ant * kNStats;
     // counters accumulate over iterations (zeroed when the ant buffers are made)
     st[kStAco] += W.aco; st[kStNew] += W.new_edges; st[kStBackup] += W.backup;
     st[kStGlobal] += W.global; st[kStCheck] += W.nchk; st[kStPops] += S.pops;
     st[kStMoves2] += S.moves2; st[kStMovesOr] += S.movesor; st[kStFlip] += S.flip;
     st[kStVerify] += S.verify;
+    if (!SEGS && A.segs) st[kStRedo] += 1;
+    st[kStStartNs] = (int64_t)t_start;
+    st[kStDurNs] = (int64_t)(global_ns() - t_start);
+    st[kStConsNs] = (int64_t)(t_cons - t_start);
+    st[kStFallNs] = W.fall_ns;
   }
 }
 
 }  // namespace
 
+size_t ants_smem_per_warp(int n, int seg_cap, bool segs) {
+  const size_t vis_bytes = ((size_t)((n + 31) >> 5) * 4 + 15) & ~(size_t)15;
+  return segs ? vis_bytes + segtab_bytes(seg_cap) : vis_bytes;
+}
+
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s) {
   const int warps = 4;
-  const int words = (C.n + 31) >> 5;
-  const size_t smem = A.smem_vis ? (size_t)warps * words * sizeof(uint32_t) : 0;
   const dim3 grid((A.m + warps - 1) / warps), block(32 * warps);
-  if (C.kw == 16) {
-    k_ants<16><<<grid, block, smem, s>>>(C, A);
-  } else {
-    k_ants<32><<<grid, block, smem, s>>>(C, A);
+  cudaError_t e = cudaSuccess;
+  if (A.segs) {  // segment tables, then the array kernel for the marked ants
+    const size_t smem = warps * ants_smem_per_warp(C.n, A.seg_cap, true);
+    if (C.kw == 16)
+      k_ants<16, true><<<grid, block, smem, s>>>(C, A);
+    else
+      k_ants<32, true><<<grid, block, smem, s>>>(C, A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  const size_t smem = A.smem_vis ? warps * ants_smem_per_warp(C.n, 0, false) : 0;
+  if (C.kw == 16)
+    k_ants<16, false><<<grid, block, smem, s>>>(C, A);
+  else
+    k_ants<32, false><<<grid, block, smem, s>>>(C, A);
   return cudaGetLastError();
 }
 
-cudaError_t prepare_ants_kernel(int kw, size_t smem) {
-  if (kw == 16) return cudaFuncSetAttribute(k_ants<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(k_ants<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr) {
+  cudaError_t e;
+  if (kw == 16) {
+    e = cudaFuncSetAttribute(k_ants<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ants<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+  } else {
+    e = cudaFuncSetAttribute(k_ants<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ants<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+  }
+  return e;
 }
 
 }  // namespace faco

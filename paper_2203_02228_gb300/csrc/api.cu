@@ -36,6 +36,8 @@ struct faco_ctx {
   int32_t* init_route = nullptr;
   int64_t init_len = 0;
   int64_t* len_tmp = nullptr;
+  int32_t* tmp_route = nullptr;          // iteration-best tour, materialised
+  int32_t* tmp_pos = nullptr;
   Ants A{};
   std::vector<void*> ant_allocs;
   cudaGraphExec_t gexec = nullptr;       // whole iteration
@@ -50,8 +52,9 @@ struct faco_ctx {
   std::vector<void*> allocs;
 };
 
-// Kernels per iteration: ants, best, source, rows, prefix sums.
-constexpr int kItersKernels = 5;
+// Kernels per iteration: ants (segment tables), ants (arrays), best,
+// best tour, source, rows, prefix sums; one fewer without segment tables.
+constexpr int kItersKernels = 7;
 // Kernels of the set-up: bbox, cell count, cell scan, cell fill, kNN,
 // nearest-neighbour tour, positions, initial local search, tour length,
 // state, positions (source), positions (best), rows, prefix sums.
@@ -106,6 +109,7 @@ int check_params(const faco_params& p) {
   if (!(p.p_best > 0.0 && p.p_best < 1.0)) return FACO_E_ARG;
   if (!(p.p_source_gb >= 0.0 && p.p_source_gb <= 1.0)) return FACO_E_ARG;
   if (p.min_new_edges < 1 || p.bl_size < 0 || p.bl_size > 128) return FACO_E_ARG;
+  if (p.seg_cap < -1 || (p.seg_cap > 0 && p.seg_cap < 8) || p.seg_cap > 4096) return FACO_E_ARG;
   return FACO_OK;
 }
 
@@ -212,6 +216,8 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     DA(L, c->st, 1);
     DA(L, c->init_route, n);
     DA(L, c->len_tmp, 1);
+    DA(L, c->tmp_route, n);
+    DA(L, c->tmp_pos, n);
     CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
     cudaStream_t s = c->stream;
     CK(cudaMemcpyAsync(c->xy, coords, sizeof(int2) * (size_t)n,
@@ -305,6 +311,23 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
   return FACO_OK;
 }
 
+// Segments per ant table: the requested size, or (auto) the largest that
+// lets two blocks of four ants share an SM (one block when the visited bits
+// are large), capped at 1024; 0 when not even 128 fit (arrays only).
+int seg_capacity(int n, int requested) {
+  if (requested >= 0) return requested;
+  const size_t base = ants_smem_per_warp(n, 0, true);
+  const size_t per_seg = ants_smem_per_warp(n, 1, true) - base;
+  const size_t budgets[2] = {110 * 1024 / 4, 220 * 1024 / 4};
+  for (size_t b : budgets) {
+    if (b <= base) continue;
+    size_t cap = (b - base) / per_seg;
+    cap = cap > 1024 ? 1024 : (cap & ~(size_t)31);
+    if (cap >= (b == budgets[0] ? 256 : 128)) return (int)cap;
+  }
+  return 0;
+}
+
 int ensure_ants(faco_ctx* c, int m) {
   if (c->A.m == m) return FACO_OK;
   CK(cudaStreamSynchronize(c->stream));
@@ -325,10 +348,21 @@ int ensure_ants(faco_ctx* c, int m) {
   DA(L, A.logb, mn);
   CK(cudaMemsetAsync(A.flags, 0, mn, c->stream));
   CK(cudaMemsetAsync(A.stats, 0, sizeof(int64_t) * m * kNStats, c->stream));
-  const size_t smem = 4 * words * sizeof(uint32_t);
-  A.smem_vis = smem <= 200 * 1024 ? 1 : 0;
+  // array kernel: visited bits in shared memory when four warps' worth fits
+  const size_t smem_arr = 4 * ants_smem_per_warp(n, 0, false);
+  A.smem_vis = smem_arr <= 200 * 1024 ? 1 : 0;
   if (!A.smem_vis) DA(L, A.vis_g, (size_t)m * words);
-  CK(prepare_ants_kernel(c->kw, A.smem_vis ? smem : 0));
+  // segment-table kernel: bits + table per warp, four warps per block
+  A.seg_cap = seg_capacity(n, c->prm.seg_cap);
+  const size_t smem_seg = A.seg_cap > 0 ? 4 * ants_smem_per_warp(n, A.seg_cap, true) : 0;
+  if (A.seg_cap > 0) {
+    DA(L, A.segs, (size_t)m * A.seg_cap);
+    DA(L, A.nseg, m);
+    DA(L, A.redo, m);
+    CK(cudaMemsetAsync(A.redo, 0, sizeof(int32_t) * m, c->stream));
+  }
+  A.keep_tours = c->prm.keep_ant_tours;
+  CK(prepare_ants_kernel(c->kw, smem_seg, A.smem_vis ? smem_arr : 0));
   if (c->prm.keep_pre_ls) {
     DA(L, A.pre_route, mn);
     DA(L, A.pre_len, m);
@@ -345,7 +379,7 @@ int enqueue_iteration(faco_ctx* c, int parts) {
   if (parts & 1) CK(launch_ants(C, c->A, c->stream));
   if (parts & 2) {
     CK(launch_best(C, c->A, c->stream));
-    CK(launch_source(C, c->A, c->stream));
+    CK(launch_source(C, c->A, c->tmp_route, c->tmp_pos, c->stream));
     CK(launch_rows(C, 1, c->stream));
     CK(launch_scan_P(C, c->stream));
   }
@@ -410,6 +444,7 @@ int faco_params_default(faco_params* p) {
   p->verify_pass = 1;
   p->keep_ant_tours = 0;
   p->keep_pre_ls = 0;
+  p->seg_cap = -1;
   p->stream = nullptr;
   return FACO_OK;
 }
@@ -453,7 +488,7 @@ int faco_iterate(faco_ctx* c, int32_t ants, int32_t budget) {
     }
   }
   c->iters_enqueued += budget;
-  c->launches += (int64_t)kItersKernels * budget;
+  c->launches += (int64_t)(c->A.seg_cap > 0 ? kItersKernels : kItersKernels - 1) * budget;
   return FACO_OK;
 }
 
@@ -531,9 +566,11 @@ int faco_stats_get(faco_ctx* c, faco_stats* s) {
       s->moves_2opt += r[kStMoves2];
       s->moves_or += r[kStMovesOr];
       s->flip_elems += r[kStFlip];
+      s->redone_ants += r[kStRedo];
     }
   }
   s->kernel_launches = c->launches;
+  s->seg_cap = c->A.seg_cap;
   return FACO_OK;
 }
 
@@ -644,6 +681,15 @@ int faco_get_ant_pre(faco_ctx* c, int32_t* tours, int64_t* lens, int32_t* checkl
   if (lens) CK(cudaMemcpy(lens, c->A.pre_len, sizeof(int64_t) * c->A.m, cudaMemcpyDeviceToHost));
   if (checklists) CK(cudaMemcpy(checklists, c->A.pre_chk, sizeof(int32_t) * mn, cudaMemcpyDeviceToHost));
   if (nchecks) CK(cudaMemcpy(nchecks, c->A.pre_nchk, sizeof(int32_t) * c->A.m, cudaMemcpyDeviceToHost));
+  return FACO_OK;
+}
+
+int faco_get_ant_stats(faco_ctx* c, int64_t* stats) {
+  if (!c || !stats) return FACO_E_ARG;
+  if (c->A.m == 0) return FACO_E_STATE;
+  int rc = sync_and_check(c);
+  if (rc != FACO_OK) return rc;
+  CK(cudaMemcpy(stats, c->A.stats, sizeof(int64_t) * kNStats * c->A.m, cudaMemcpyDeviceToHost));
   return FACO_OK;
 }
 

@@ -152,26 +152,60 @@ __global__ void __launch_bounds__(1024) k_best(Colony C, Ants A) {
   }
 }
 
+// The iteration-best tour as explicit route/pos (into tmp): from its
+// segment table (source positions -> node ids of the current source), or
+// from the ant's arrays when it was built with them.  Skipped when neither
+// the global best nor the source will take it.
+__global__ void k_best_tour(Colony C, Ants A, int32_t* tmp_route, int32_t* tmp_pos) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = C.n;
+  const DevState* st = C.st;
+  if (t >= n || (!st->gb_improved && st->use_gb)) return;
+  const int a = st->it_best_ant;
+  int node;
+  const int S = A.nseg ? A.nseg[a] : -1;
+  if (S < 0) {
+    node = A.route[(size_t)a * n + t];
+  } else {
+    const int4* sg = A.segs + (size_t)a * A.seg_cap;
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sg[mid].z <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int4 s = sg[lo];
+    const int d = t - s.z;
+    int q = s.w ? s.x + s.y - 1 - d : s.x + d;
+    if ((unsigned)q >= (unsigned)n) {  // inconsistent table: a library bug, flagged
+      atomicOr(&C.st->error, kErrInternal);
+      q = 0;
+    }
+    node = C.src_route[q];
+  }
+  tmp_route[t] = node;
+  tmp_pos[node] = t;
+}
+
 // Global best <- iteration best when improved; source <- global best or
 // iteration best (routes and positions).
-__global__ void k_source(Colony C, Ants A) {
+__global__ void k_source(Colony C, const int32_t* tmp_route, const int32_t* tmp_pos) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = C.n;
   if (i >= n) return;
   const DevState* st = C.st;
-  const int a = st->it_best_ant;
-  const int32_t r = A.route[(size_t)a * n + i];
-  const int32_t p = A.pos[(size_t)a * n + i];
   if (st->gb_improved) {
-    C.gb_route[i] = r;
-    C.gb_pos[i] = p;
+    C.gb_route[i] = tmp_route[i];
+    C.gb_pos[i] = tmp_pos[i];
   }
   if (st->use_gb) {
     C.src_route[i] = C.gb_route[i];
     C.src_pos[i] = C.gb_pos[i];
   } else {
-    C.src_route[i] = r;
-    C.src_pos[i] = p;
+    C.src_route[i] = tmp_route[i];
+    C.src_pos[i] = tmp_pos[i];
   }
 }
 
@@ -223,8 +257,10 @@ cudaError_t launch_best(const Colony& C, const Ants& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_source(const Colony& C, const Ants& A, cudaStream_t s) {
-  k_source<<<(C.n + 255) / 256, 256, 0, s>>>(C, A);
+cudaError_t launch_source(const Colony& C, const Ants& A, int32_t* tmp_route, int32_t* tmp_pos,
+                          cudaStream_t s) {
+  k_best_tour<<<(C.n + 255) / 256, 256, 0, s>>>(C, A, tmp_route, tmp_pos);
+  k_source<<<(C.n + 255) / 256, 256, 0, s>>>(C, tmp_route, tmp_pos);
   return cudaGetLastError();
 }
 

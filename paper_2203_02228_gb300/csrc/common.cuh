@@ -24,7 +24,12 @@ enum : int32_t {
 // Per-ant counters (row of Ants::stats).
 enum : int {
   kStAco = 0, kStNew, kStBackup, kStGlobal, kStCheck, kStPops, kStMoves2, kStMovesOr,
-  kStFlip, kStVerify, kNStats = 16
+  kStFlip, kStVerify, kStRedo,
+  kStStartNs,  // device time (ns) when the ant's warp started, last iteration
+  kStDurNs,    // its duration (ns), last iteration
+  kStConsNs,   // of which construction (ns), last iteration
+  kStFallNs,   // of which global nearest-unvisited scans (ns), last iteration
+  kNStats = 16
 };
 
 // Colony scalars that change on the device (read by graph-replayed kernels).
@@ -84,7 +89,12 @@ struct Ants {
   uint8_t* flags;        // [m][n] bit0 queued, bit1 popped this round (kept zero between uses)
   int32_t* logb;         // [m][n] nodes popped this round, first pop order
   uint32_t* vis_g;       // [m][words] visited bits when they do not fit shared memory
-  int32_t smem_vis;      // 1: visited bits live in shared memory
+  int32_t smem_vis;      // 1: visited bits live in shared memory (array kernel)
+  int32_t seg_cap;       // segments per ant table (0: arrays only)
+  int4* segs;            // [m][seg_cap] final tours as (lo, len, off, rev), or null
+  int32_t* nseg;         // [m] segment count, -1 when the tour is in route/pos
+  int32_t* redo;         // [m] 1: the table overflowed, the array kernel redoes the ant
+  int32_t keep_tours;    // 1: also write every tour to route[] (inspection)
   int32_t* pre_route;    // [m][n] optional: tours before local search
   int64_t* pre_len;      // [m]
   int32_t* pre_chk;      // [m][n]
@@ -175,6 +185,12 @@ __device__ __forceinline__ int roulette(const float (&w)[W], float u) {
 // Small warp helpers.
 // ---------------------------------------------------------------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
   return (int64_t)__shfl_sync(kFull, (unsigned long long)v, src);

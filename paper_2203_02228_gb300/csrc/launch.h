@@ -10,13 +10,15 @@ namespace faco {
 
 // ants.cu
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s);
-cudaError_t prepare_ants_kernel(int kw, size_t smem);
+cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr);
+size_t ants_smem_per_warp(int n, int seg_cap, bool segs);
 
 // colony.cu
 cudaError_t launch_rows(const Colony& C, int update, cudaStream_t s);
 cudaError_t launch_scan_P(const Colony& C, cudaStream_t s);
 cudaError_t launch_best(const Colony& C, const Ants& A, cudaStream_t s);
-cudaError_t launch_source(const Colony& C, const Ants& A, cudaStream_t s);
+cudaError_t launch_source(const Colony& C, const Ants& A, int32_t* tmp_route, int32_t* tmp_pos,
+                          cudaStream_t s);
 cudaError_t launch_state_init(const Colony& C, const int64_t* len, cudaStream_t s);
 cudaError_t launch_positions(const int32_t* route, int32_t* pos, int n, cudaStream_t s);
 cudaError_t launch_tour_length(const int2* xy, const int32_t* route, int n, int64_t* out,

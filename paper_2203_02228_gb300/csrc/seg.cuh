@@ -33,14 +33,14 @@ struct SegTab {
   uint16_t* B;       // [cap] ids in source order
   int32_t* offA;     // [cap] sg[A[r]].off
   int32_t* loB;      // [cap] sg[B[r]].lo
-  uint16_t* tmp;     // [cap] scratch
+  uint16_t* tmp;     // [2 * cap + 2] scratch
   int32_t* S;        // segment count (shared)
   int cap;
 };
 
 // bytes of shared memory per warp for a table of `cap` segments
 __host__ __device__ constexpr size_t segtab_bytes(int cap) {
-  return (size_t)cap * (sizeof(Seg) + 3 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 16;
+  return (size_t)cap * (sizeof(Seg) + 4 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 2 * sizeof(uint16_t) + 16;
 }
 
 __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
@@ -56,8 +56,8 @@ __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
   T.B = reinterpret_cast<uint16_t*>(p);
   p += (size_t)cap * sizeof(uint16_t);
   T.tmp = reinterpret_cast<uint16_t*>(p);
-  p += (size_t)cap * sizeof(uint16_t);
-  T.S = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+  p += (size_t)(2 * cap + 2) * sizeof(uint16_t);
+  T.S =reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
   T.cap = cap;
   return T;
 }
@@ -209,16 +209,21 @@ struct SegTour {
   const int2* xy;       // coordinates by source position
   const int32_t* cn;    // candidate source positions by source position [n][kw]
 
+  // Lookups stay in [0, n) even if the table were inconsistent (which would
+  // be a library bug: it is flagged and shows up as a wrong tour, not as an
+  // out-of-range access).
   __device__ __forceinline__ int pos_of(int q) const {
     const int r = bsearch_le(T.loB, *T.S, q);
     const Seg s = T.sg[T.B[r]];
-    return s.off + (s.rev ? s.lo + s.len - 1 - q : q - s.lo);
+    const int t = s.off + (s.rev ? s.lo + s.len - 1 - q : q - s.lo);
+    return (unsigned)t < (unsigned)n ? t : 0;
   }
   __device__ __forceinline__ int at(int t) const {
     const int r = bsearch_le(T.offA, *T.S, t);
     const Seg s = T.sg[T.A[r]];
     const int d = t - s.off;
-    return s.rev ? s.lo + s.len - 1 - d : s.lo + d;
+    const int q = s.rev ? s.lo + s.len - 1 - d : s.lo + d;
+    return (unsigned)q < (unsigned)n ? q : 0;
   }
   __device__ __forceinline__ int2 coord(int q) const { return xy[q]; }
   __device__ __forceinline__ int cand(int q, int s) const { return cn[(size_t)q * kw + s]; }

@@ -129,13 +129,21 @@ CASES = [
 ]
 
 
+# Tour representation of the ants: "auto" = segment tables sized from shared
+# memory, "arrays" = explicit route/pos for every ant, "tiny" = 8-segment
+# tables, so that most ants overflow and are redone on arrays.
+MODES = {"auto": -1, "arrays": 0, "tiny": 8}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("name,n,ants,iters,k,extra", CASES, ids=[c[0] for c in CASES])
-def test_iterations_bit_exact(name, n, ants, iters, k, extra):
+def test_iterations_bit_exact(name, n, ants, iters, k, extra, mode):
     if name.startswith("stippled"):
         xy = inputs.stippled(n, seed=n, blobs=10, ridges=2, side=60000)
     else:
         xy = inputs.uniform(n, seed=1000 + n, side=1_000_000 if n > 16 else 1000)
-    g, o = make_pair(xy, k, **extra)
+    g = Colony(xy, k, keep_ant_tours=1, keep_pre_ls=1, seg_cap=MODES[mode], **extra)
+    o = oracle.Colony(xy, k, keep_pre_ls=1, threads=8, **extra)
     o_hist = []
     for it in range(iters):
         g.iterate(ants, 1)
@@ -165,6 +173,50 @@ def test_budget_in_one_call_equals_single_steps():
     np.testing.assert_array_equal(a.history(), b.history())
     assert np.array_equal(a.tau().view(np.uint32), b.tau().view(np.uint32))
     np.testing.assert_array_equal(a.best()[0], b.best()[0])
+
+
+def test_stippled20k_segments_bit_exact():
+    """A mid-size clustered instance where the per-ant segment tables see
+    hundreds of reversals: every ant length, the history and the state."""
+    xy = inputs.stippled(20000, seed=2020, blobs=24, ridges=4, side=100_000)
+    g = Colony(xy, 16, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, threads=16)
+    o_hist = []
+    for it in range(12):
+        g.iterate(48, 1)
+        oh, oal = o.iterate(48, 1)
+        o_hist.append(oh[0])
+        np.testing.assert_array_equal(g.ant_tours()[1], oal[0], err_msg="iteration %d" % (it + 1))
+    np.testing.assert_array_equal(g.history(), np.array(o_hist))
+    assert_same_state(g, o, 48)
+    st = g.stats()
+    assert st.moves_2opt > 0 and st.moves_or > 0
+
+
+def test_stippled100k_setup_and_first_iterations():
+    """The n = 100,000 stippled workload at full size in the benchmark's
+    launch configuration (1,024 ants): lists, initial tour, limits and the
+    first two iterations of every ant, bit for bit."""
+    xy = inputs.workload_points("stippled100k")
+    g = Colony(xy, 16, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, threads=16)
+    gc, gb, ge = g.lists()
+    oc, ob, oe = o.lists()
+    np.testing.assert_array_equal(gc, oc)
+    np.testing.assert_array_equal(gb, ob)
+    assert np.array_equal(ge.view(np.uint32), oe.view(np.uint32))
+    assert g.initial()[1] == o.initial()[1]
+    np.testing.assert_array_equal(g.initial()[0], o.initial()[0])
+    for it in range(2):
+        g.iterate(1024, 1)
+        oh, oal = o.iterate(1024, 1)
+        gt, gl = g.ant_tours()
+        np.testing.assert_array_equal(gl, oal[0])
+        ot, _ = o.ant_tours()
+        sample = np.arange(0, 1024, 97)
+        np.testing.assert_array_equal(gt[sample], ot[sample])
+    np.testing.assert_array_equal(g.history()[-1], oh[0])
+    assert_same_state(g, o, 1024)
 
 
 def test_uniform1k_full_workload_bit_exact():
