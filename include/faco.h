@@ -181,10 +181,13 @@ int faco_get_history(faco_ctx* c, int64_t* hist, int64_t max_iters, int64_t* row
 int faco_get_ant_tours(faco_ctx* c, int32_t* tours, int64_t* lens);
 int faco_get_ant_pre(faco_ctx* c, int32_t* tours, int64_t* lens, int32_t* checklists,
                      int32_t* nchecks);
-/* Per-ant counters (ants x 16 int64, accumulated over the iterations run
- * with the current ant count): select_next_node calls, new edges, backup
- * picks, global picks, checklist length, queue pops, 2-opt moves, Or-opt
- * moves, reversed elements, verify rounds, redone on arrays, 0 x 5. */
+/* Per-ant counters (ants x 24 int64).  Columns 0-10 accumulate over the
+ * iterations run with the current ant count: select_next_node calls, new
+ * edges, backup picks, global picks, checklist length, queue pops, 2-opt
+ * moves, Or-opt moves, reversed elements, verify rounds, redone on arrays.
+ * Columns 11-18 are device timer readings (ns) of the last iteration: start,
+ * duration, construction, nearest-unvisited scans, local-search evaluation,
+ * pop confirmation, move application, endpoint queueing.  19-23: zero. */
 int faco_get_ant_stats(faco_ctx* c, int64_t* stats);
 
 /* ---- device self-test hook (used by the test-suite) ----------------------

@@ -187,7 +187,7 @@ class Colony:
 
     def ant_stats(self) -> np.ndarray:
         m = self.stats().ants
-        st = np.zeros((m, 16), np.int64)
+        st = np.zeros((m, 24), np.int64)
         _lib.check(self._L.faco_get_ant_stats(self._h, _ptr(st)), "faco_get_ant_stats")
         return st
 

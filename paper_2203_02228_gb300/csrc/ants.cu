@@ -33,6 +33,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "ls.cuh"
+#include "nearest.cuh"
 #include "seg.cuh"
 
 namespace faco {
@@ -244,9 +245,17 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
       return __shfl_sync(kFull, q, __ffs(bal) - 1);
     }
   }
-  // global nearest unvisited node: scan visited words, skip full ones
+  // global nearest unvisited node: rings of grid cells around u, else a
+  // scan of the visited words that skips full ones
   const uint64_t t0 = global_ns();
   const int2 xu = C.XYsrc[pc];
+  const int near = ring_nearest(C.xy, C.grid, C.cell_start, C.cell_pts, xu, 24,
+                                [&](int v) { return vis_get(vis, C.src_pos[v]); });
+  if (near >= 0) {
+    W.global++;
+    W.fall_ns += (int64_t)(global_ns() - t0);
+    return C.src_pos[near];
+  }
   uint64_t bk = ~0ull;
   int32_t bi = INT_MAX;
   const int words = (n + 31) >> 5;
@@ -451,7 +460,7 @@ __device__ void seg_finish_construction(const SegTab& T) {
 }
 
 template <int KW, bool SEGS>
-__global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
+__global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
   extern __shared__ __align__(16) char smem[];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
   const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -540,6 +549,101 @@ __global__ void __launch_bounds__(128) k_ants(Colony C, Ants A) {
   }
 }
 
+// One block of kAntWarps warps per ant, tour as a segment table in shared
+// memory: warp 0 constructs, then all warps run the local search with
+// speculative in-order pops (ls_run_block).  An ant whose table fills up is
+// marked and redone by the array kernel.
+constexpr int kAntWarps = 4;
+
+template <int KW>
+__global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ LsShared sh;
+  __shared__ int s_nchk, s_overflow;
+  __shared__ int64_t s_pre_len;
+  const int ant = blockIdx.x;
+  if (ant >= A.m) return;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int n = C.n;
+  const int words = (n + 31) >> 5;
+  const size_t vis_bytes = ((size_t)words * 4 + 15) & ~(size_t)15;
+  uint32_t* vis = reinterpret_cast<uint32_t*>(smem);
+  const SegTab tab = segtab_at(smem + vis_bytes, A.seg_cap);
+  const uint32_t iter = (uint32_t)(C.st->iter + 1);
+  const uint64_t t_start = global_ns();
+  int32_t* route = A.route + (size_t)ant * n;
+  int32_t* chk = A.chk + (size_t)ant * n;
+
+  Walk W;
+  W.segs = true;
+  W.tab = tab;
+  W.fall_ns = 0;
+  W.aco = W.backup = W.global = 0;
+  W.new_edges = W.nchk = 0;
+  uint64_t t_cons = t_start;
+  if (w == 0) {
+    if (lane == 0) *tab.S = 0;
+    __syncwarp();
+    const int64_t pre_len = construct<KW>(C, nullptr, nullptr, vis, chk, W, (uint32_t)ant, iter);
+    t_cons = global_ns();
+    if (!W.overflow) seg_finish_construction(tab);
+    if (lane == 0) {
+      s_pre_len = pre_len;
+      s_nchk = W.nchk;
+      s_overflow = W.overflow;
+    }
+    if (!W.overflow && A.pre_route) {
+      seg_materialize(C, tab, A.pre_route + (size_t)ant * n);
+      for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = C.src_route[chk[i]];
+      if (lane == 0) {
+        A.pre_len[ant] = pre_len;
+        A.pre_nchk[ant] = W.nchk;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_overflow) {
+    if (tid == 0) A.redo[ant] = 1;
+    return;
+  }
+  LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
+          A.logb + (size_t)ant * n};
+  LsStats S{0, 0, 0, 0, 0};
+  SegTour T{n, C.k, C.kw, tab, C.XYsrc, C.Csrc};
+  const int64_t gain = ls_run_block(E, T, chk, s_nchk, S, sh);
+  if (gain < 0) {  // the table filled up during the search
+    if (tid == 0) A.redo[ant] = 1;
+    return;
+  }
+  // hand the tour over: segments in ant order
+  const int Sn = *tab.S;
+  int4* out = A.segs + (size_t)ant * A.seg_cap;
+  for (int r = tid; r < Sn; r += blockDim.x) {
+    const Seg s = tab.sg[tab.A[r]];
+    out[r] = make_int4(s.lo, s.len, s.off, s.rev);
+  }
+  if (w == 0 && A.keep_tours) seg_materialize(C, tab, route);
+  if (tid == 0) {
+    A.nseg[ant] = Sn;
+    A.len[ant] = s_pre_len - gain;
+    A.redo[ant] = 0;
+    int64_t* st = A.stats + (size_t)ant * kNStats;
+    // counters accumulate over iterations (zeroed when the ant buffers are made)
+    st[kStAco] += W.aco; st[kStNew] += W.new_edges; st[kStBackup] += W.backup;
+    st[kStGlobal] += W.global; st[kStCheck] += W.nchk; st[kStPops] += S.pops;
+    st[kStMoves2] += S.moves2; st[kStMovesOr] += S.movesor; st[kStFlip] += S.flip;
+    st[kStVerify] += S.verify;
+    st[kStStartNs] = (int64_t)t_start;
+    st[kStDurNs] = (int64_t)(global_ns() - t_start);
+    st[kStConsNs] = (int64_t)(t_cons - t_start);
+    st[kStFallNs] = W.fall_ns;
+    st[kStEvalNs] = S.t_eval;
+    st[kStConfNs] = S.t_confirm;
+    st[kStFlipNs] = S.t_flip;
+    st[kStPushNs] = S.t_push;
+  }
+}
+
 }  // namespace
 
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs) {
@@ -548,18 +652,18 @@ size_t ants_smem_per_warp(int n, int seg_cap, bool segs) {
 }
 
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s) {
-  const int warps = 4;
-  const dim3 grid((A.m + warps - 1) / warps), block(32 * warps);
   cudaError_t e = cudaSuccess;
-  if (A.segs) {  // segment tables, then the array kernel for the marked ants
-    const size_t smem = warps * ants_smem_per_warp(C.n, A.seg_cap, true);
+  if (A.segs) {  // one block per ant on segment tables, then arrays for the marked ants
+    const size_t smem = ants_smem_per_warp(C.n, A.seg_cap, true);
     if (C.kw == 16)
-      k_ants<16, true><<<grid, block, smem, s>>>(C, A);
+      k_ants_blk<16><<<A.m, 32 * kAntWarps, smem, s>>>(C, A);
     else
-      k_ants<32, true><<<grid, block, smem, s>>>(C, A);
+      k_ants_blk<32><<<A.m, 32 * kAntWarps, smem, s>>>(C, A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  const int warps = 4;
+  const dim3 grid((A.m + warps - 1) / warps), block(32 * warps);
   const size_t smem = A.smem_vis ? warps * ants_smem_per_warp(C.n, 0, false) : 0;
   if (C.kw == 16)
     k_ants<16, false><<<grid, block, smem, s>>>(C, A);
@@ -571,11 +675,11 @@ cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s) {
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr) {
   cudaError_t e;
   if (kw == 16) {
-    e = cudaFuncSetAttribute(k_ants<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
+    e = cudaFuncSetAttribute(k_ants_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_ants<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
   } else {
-    e = cudaFuncSetAttribute(k_ants<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
+    e = cudaFuncSetAttribute(k_ants_blk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_ants<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
   }

@@ -38,6 +38,9 @@ struct faco_ctx {
   int64_t* len_tmp = nullptr;
   int32_t* tmp_route = nullptr;          // iteration-best tour, materialised
   int32_t* tmp_pos = nullptr;
+  Grid grid{};                           // point grid (candidate lists, nearest unvisited)
+  int32_t* cell_start = nullptr;
+  int32_t* cell_pts = nullptr;
   Ants A{};
   std::vector<void*> ant_allocs;
   cudaGraphExec_t gexec = nullptr;       // whole iteration
@@ -101,6 +104,9 @@ Colony colony_view(const faco_ctx* c) {
   C.src_route = c->src_route; C.src_pos = c->src_pos; C.gb_route = c->gb_route; C.gb_pos = c->gb_pos;
   C.Wsrc = c->Wsrc; C.Csrc = c->Csrc; C.XYsrc = c->XYsrc; C.Dsrc = c->Dsrc; C.Psrc = c->Psrc;
   C.st = c->st;
+  C.grid = c->grid;
+  C.cell_start = c->cell_start;
+  C.cell_pts = c->cell_pts;
   return C;
 }
 
@@ -253,12 +259,14 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     g.gx = (hb[2] - hb[0]) / g.cs + 1;
     g.gy = (hb[3] - hb[1]) / g.cs + 1;
     const int64_t cells = (int64_t)g.gx * g.gy;
-    int32_t *cc = nullptr, *cs = nullptr, *cp = nullptr;
-    if ((r2 = dalloc(tmp, &cc, cells)) != FACO_OK || (r2 = dalloc(tmp, &cs, cells + 1)) != FACO_OK ||
-        (r2 = dalloc(tmp, &cp, n)) != FACO_OK) {
+    int32_t* cc = nullptr;
+    if ((r2 = dalloc(tmp, &cc, cells)) != FACO_OK || (r2 = dalloc(c->allocs, &c->cell_start, cells + 1)) != FACO_OK ||
+        (r2 = dalloc(c->allocs, &c->cell_pts, n)) != FACO_OK) {
       free_tmp();
       return r2;
     }
+    c->grid = g;
+    int32_t *cs = c->cell_start, *cp = c->cell_pts;
     if (build_lists(c->xy, n, c->k, c->bl, g, cc, cs, cp, c->cand, c->backup, c->eta, s) != cudaSuccess) {
       free_tmp();
       return FACO_E_CUDA;
@@ -277,7 +285,8 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
       free_tmp();
       return r2;
     }
-    cudaError_t e = launch_nn_tour(c->xy, n, c->cand, c->k, c->backup, c->bl, c->init_route, vis_g, s);
+    cudaError_t e = launch_nn_tour(c->xy, n, c->cand, c->k, c->backup, c->bl, c->init_route, vis_g, g,
+                                   c->cell_start, c->cell_pts, s);
     if (e == cudaSuccess) e = launch_positions(c->init_route, c->src_pos, n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fl, 0, n, s);
     if (e == cudaSuccess)
@@ -311,19 +320,25 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
   return FACO_OK;
 }
 
-// Segments per ant table: the requested size, or (auto) the largest that
-// lets two blocks of four ants share an SM (one block when the visited bits
-// are large), capped at 1024; 0 when not even 128 fit (arrays only).
-int seg_capacity(int n, int requested) {
+// Segments per ant table (one ant per block): the requested size, or (auto)
+// the largest table, up to 1024 segments, that still lets every ant of an
+// iteration be resident at once; with fewer blocks per SM when the visited
+// bits alone are too large for that.  0 (arrays only) when not even 64 fit.
+int seg_capacity(int n, int m, int requested) {
   if (requested >= 0) return requested;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t base = ants_smem_per_warp(n, 0, true);
   const size_t per_seg = ants_smem_per_warp(n, 1, true) - base;
-  const size_t budgets[2] = {110 * 1024 / 4, 220 * 1024 / 4};
-  for (size_t b : budgets) {
-    if (b <= base) continue;
-    size_t cap = (b - base) / per_seg;
+  const size_t total = 225 * 1024, fixed = 2 * 1024;  // usable per SM; static + reserved per block
+  const int want = (m + sms - 1) / (sms > 0 ? sms : 1);
+  for (int bps = want; bps >= 1; --bps) {
+    const size_t budget = total / bps - fixed;
+    if (budget <= base) continue;
+    size_t cap = (budget - base) / per_seg;
     cap = cap > 1024 ? 1024 : (cap & ~(size_t)31);
-    if (cap >= (b == budgets[0] ? 256 : 128)) return (int)cap;
+    if (cap >= 256 || (bps == 1 && cap >= 64)) return (int)cap;
   }
   return 0;
 }
@@ -352,9 +367,9 @@ int ensure_ants(faco_ctx* c, int m) {
   const size_t smem_arr = 4 * ants_smem_per_warp(n, 0, false);
   A.smem_vis = smem_arr <= 200 * 1024 ? 1 : 0;
   if (!A.smem_vis) DA(L, A.vis_g, (size_t)m * words);
-  // segment-table kernel: bits + table per warp, four warps per block
-  A.seg_cap = seg_capacity(n, c->prm.seg_cap);
-  const size_t smem_seg = A.seg_cap > 0 ? 4 * ants_smem_per_warp(n, A.seg_cap, true) : 0;
+  // segment-table kernel: one ant per block, bits + table in shared memory
+  A.seg_cap = seg_capacity(n, m, c->prm.seg_cap);
+  const size_t smem_seg = A.seg_cap > 0 ? ants_smem_per_warp(n, A.seg_cap, true) : 0;
   if (A.seg_cap > 0) {
     DA(L, A.segs, (size_t)m * A.seg_cap);
     DA(L, A.nseg, m);

@@ -29,7 +29,11 @@ enum : int {
   kStDurNs,    // its duration (ns), last iteration
   kStConsNs,   // of which construction (ns), last iteration
   kStFallNs,   // of which global nearest-unvisited scans (ns), last iteration
-  kNStats = 16
+  kStEvalNs,   // local search: evaluation rounds (ns), last iteration
+  kStConfNs,   //   confirming pops (ns)
+  kStFlipNs,   //   applying moves (ns)
+  kStPushNs,   //   queueing endpoints (ns)
+  kNStats = 24
 };
 
 // Colony scalars that change on the device (read by graph-replayed kernels).
@@ -49,6 +53,11 @@ struct DevState {
   int32_t pad;
   int64_t* hist;         // per-iteration history, 4 int64 per row
   int64_t hist_cap;      // rows available
+};
+
+// Uniform grid over the points: square cells of side cs from (minx, miny).
+struct Grid {
+  int32_t minx, miny, cs, gx, gy;
 };
 
 // Device pointers and sizes of one colony (passed by value).
@@ -75,6 +84,9 @@ struct Colony {
   int32_t* Dsrc;         // [n] length of source edge (p, p+1)
   int64_t* Psrc;         // [n+1] exclusive prefix sums of Dsrc
   DevState* st;
+  Grid grid;             // point grid of the candidate-list build
+  const int32_t* cell_start;  // [cells+1]
+  const int32_t* cell_pts;    // [n] node ids by cell
 };
 
 // Per-ant buffers of one ant count.
@@ -144,13 +156,23 @@ __device__ __forceinline__ uint64_t sqdist(int2 a, int2 b) {
 }
 
 __device__ __forceinline__ int32_t euc2d_m(uint64_t m) {
-  uint64_t r = (uint64_t)__fsqrt_rn(__ull2float_rn(m));
-  while (r * r > m) --r;
-  while ((r + 1) * (r + 1) <= m) ++r;
-  return (int32_t)(r + ((m - r * r) > r ? 1u : 0u));
+  uint32_t r = (uint32_t)__fsqrt_rn(__ull2float_rn(m));  // within 2 of floor(sqrt(m))
+  uint64_t rr = (uint64_t)r * r;
+  while (rr > m) {
+    --r;
+    rr = (uint64_t)r * r;
+  }
+  while (rr + 2ull * r + 1ull <= m) {
+    rr += 2ull * r + 1ull;
+    ++r;
+  }
+  return (int32_t)(r + ((m - rr) > r ? 1u : 0u));
 }
 
-__device__ __forceinline__ int32_t euc2d(int2 a, int2 b) { return euc2d_m(sqdist(a, b)); }
+__device__ __forceinline__ int32_t euc2d(int2 a, int2 b) {
+  const int32_t dx = a.x - b.x, dy = a.y - b.y;  // |dx|, |dy| < 2^24
+  return euc2d_m((uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy));
+}
 
 // ---------------------------------------------------------------------
 // Roulette of Eq. 1 over W slots (weights tau*eta, zero when visited or

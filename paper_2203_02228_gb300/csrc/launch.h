@@ -25,9 +25,6 @@ cudaError_t launch_tour_length(const int2* xy, const int32_t* route, int n, int6
                                cudaStream_t s);
 
 // knn.cu
-struct Grid {
-  int32_t minx, miny, cs, gx, gy;
-};
 cudaError_t launch_bbox_check(const int2* xy, int n, int32_t* out5, cudaStream_t s);
 cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int32_t* cell_count,
                         int32_t* cell_start, int32_t* cell_pts, int32_t* cand, int32_t* backup,
@@ -35,7 +32,8 @@ cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int
 
 // tour.cu
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
-                           int bl, int32_t* route, uint32_t* vis_g, cudaStream_t s);
+                           int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
+                           const int32_t* cpts, cudaStream_t s);
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, int k, int oropt, int verify,
                            int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s);

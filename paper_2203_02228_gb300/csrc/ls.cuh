@@ -23,9 +23,11 @@
 //              -- reversed first, then kept; u, v outside the segment and
 //              {pred a, succ e}; applied as two or three edge exchanges.
 //
-// A Tour provides (device): n, k; pos_of(x) and at(t) (lane-local lookups);
-// coord(x); cand(x, s); flip(x, y, S) (warp-collective; false when the
-// representation ran out of capacity).
+// A Tour provides (device, lane-local unless noted): n, k; pos_of(x);
+// succ(x), pred(x); nbrs(x, pred, succ); walk(a, pred, s1, s2, s3) (the
+// predecessor and three successors); coord(x); cand(x, s); and the
+// warp-collective flip(x, y, S) (false when the representation ran out of
+// capacity).
 #pragma once
 
 #include <climits>
@@ -43,6 +45,7 @@ struct LsEnv {
 
 struct LsStats {
   int64_t pops, moves2, movesor, flip, verify;
+  int64_t t_eval, t_confirm, t_flip, t_push;  // device ns per phase (block search)
 };
 
 // Explicit tour: route[t] = node at position t, pos = inverse.
@@ -53,12 +56,31 @@ struct ArrTour {
   const int2* xy;       // node-indexed coordinates
   const int32_t* cn;    // node-indexed candidate lists [n][k]
   __device__ __forceinline__ int pos_of(int x) const { return pos[x]; }
-  __device__ __forceinline__ int at(int t) const { return route[t]; }
+  __device__ __forceinline__ int at_off(int p, int d) const {
+    p += d;
+    if (p >= n) p -= n;
+    if (p < 0) p += n;
+    return route[p];
+  }
+  __device__ __forceinline__ int succ(int x) const { return at_off(pos[x], 1); }
+  __device__ __forceinline__ int pred(int x) const { return at_off(pos[x], -1); }
+  __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
+    const int t = pos[x];
+    p = at_off(t, -1);
+    s = at_off(t, 1);
+  }
+  __device__ __forceinline__ void walk(int a, int& p, int& s1, int& s2, int& s3) const {
+    const int t = pos[a];
+    p = at_off(t, -1);
+    s1 = at_off(t, 1);
+    s2 = at_off(t, 2);
+    s3 = at_off(t, 3);
+  }
   __device__ __forceinline__ int2 coord(int x) const { return xy[x]; }
   __device__ __forceinline__ int cand(int x, int s) const { return cn[(size_t)x * k + s]; }
 
   // Reverse the forward span x..y (or its complement when longer than n/2).
-  __device__ __noinline__ bool flip(int x, int y, LsStats& S) {
+  __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {
     const int lane = lane_id();
     int i = pos[x], j = pos[y];
     int L = j - i;
@@ -104,35 +126,22 @@ struct ArrTour {
   }
 };
 
-template <class Tour>
-__device__ __forceinline__ int tour_succ(const Tour& T, int x) {
-  const int p = T.pos_of(x) + 1;
-  return T.at(p == T.n ? 0 : p);
-}
-
-template <class Tour>
-__device__ __forceinline__ int tour_pred(const Tour& T, int x) {
-  const int p = T.pos_of(x) - 1;
-  return T.at(p < 0 ? T.n - 1 : p);
-}
-
 // Exchange tour edges {n1,n2},{n3,n4} for {n1,n3},{n2,n4}: with n1->n2 a
 // forward edge this is the Alg 3 move (n1,n2,n3,n4) -> flip n2..n3,
 // otherwise the move (n2,n1,n4,n3) -> flip n1..n4.
 template <class Tour>
 __device__ __forceinline__ bool tour_move2(Tour& T, int n1, int n2, int n3, int n4, LsStats& S) {
-  if (tour_succ(T, n1) == n2) return T.flip(n2, n3, S);
+  if (T.succ(n1) == n2) return T.flip(n2, n3, S);
   return T.flip(n1, n4, S);
 }
 
 // Best improving 2-opt move from a; returns the gain (0: none) and the move
 // (w,x,y,z) with w->x and y->z removed, flip x..y.
 template <class Tour>
-__device__ __noinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
-  const int n = T.n, k = T.k, lane = lane_id();
-  const int apos = T.pos_of(a);
-  const int a_succ = T.at(apos + 1 == n ? 0 : apos + 1);
-  const int a_pred = T.at(apos == 0 ? n - 1 : apos - 1);
+__device__ __forceinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
+  const int k = T.k, lane = lane_id();
+  int a_pred, a_succ;
+  T.nbrs(a, a_pred, a_succ);
   const int2 xa = T.coord(a), xs = T.coord(a_succ), xp = T.coord(a_pred);
   const int d_as = euc2d(xa, xs), d_ap = euc2d(xp, xa);
   int64_t best = 0;
@@ -144,8 +153,7 @@ __device__ __noinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
     int64_t g = 0;
     if (s < k) {
       const int b = T.cand(a, s);
-      const int bp = T.pos_of(b);
-      const int bn = side == 0 ? T.at(bp + 1 == n ? 0 : bp + 1) : T.at(bp == 0 ? n - 1 : bp - 1);
+      const int bn = side == 0 ? T.succ(b) : T.pred(b);
       const int2 xb = T.coord(b), xbn = T.coord(bn);
       const int d_ab = euc2d(xa, xb);
       if (side == 0) {
@@ -169,9 +177,9 @@ __device__ __noinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
     const int side = bidx / k, s = bidx % k;
     const int b = T.cand(a, s);
     if (side == 0) {
-      mv[0] = a; mv[1] = a_succ; mv[2] = b; mv[3] = tour_succ(T, b);
+      mv[0] = a; mv[1] = a_succ; mv[2] = b; mv[3] = T.succ(b);
     } else {
-      mv[0] = a_pred; mv[1] = a; mv[2] = tour_pred(T, b); mv[3] = b;
+      mv[0] = a_pred; mv[1] = a; mv[2] = T.pred(b); mv[3] = b;
     }
   }
   return best;
@@ -180,17 +188,11 @@ __device__ __noinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
 // Best improving Or-opt move from a (definition in the file comment).
 // mv = {p, a, e, q, u, v, kept}.
 template <class Tour>
-__device__ __noinline__ int64_t eval_or(const Tour& T, int a, int mv[7]) {
+__device__ __forceinline__ int64_t eval_or(const Tour& T, int a, int mv[7]) {
   const int n = T.n, k = T.k, lane = lane_id();
   if (n < 8) return 0;
-  const int apos = T.pos_of(a);
-  auto at = [&](int off) {
-    int p = apos + off;
-    if (p >= n) p -= n;
-    if (p < 0) p += n;
-    return T.at(p);
-  };
-  const int p = at(-1), s1 = at(1), s2 = at(2), s3 = at(3);
+  int p, s1, s2, s3;
+  T.walk(a, p, s1, s2, s3);
   const int2 xa = T.coord(a), xp = T.coord(p), x1 = T.coord(s1), x2 = T.coord(s2), x3 = T.coord(s3);
   const int d_pa = euc2d(xp, xa);
   // l = 1: e = a, q = s1;  l = 2: e = s1, q = s2;  l = 3: e = s2, q = s3
@@ -205,41 +207,45 @@ __device__ __noinline__ int64_t eval_or(const Tour& T, int a, int mv[7]) {
     const int s = k <= 16 ? (lane & 15) : lane;
     if (s < k) {
       const int b = T.cand(a, s);
-      const int bp = T.pos_of(b);
       int u, v;
       if (side == 0) {
         u = b;
-        v = T.at(bp + 1 == n ? 0 : bp + 1);
+        v = T.succ(b);
       } else {
-        u = T.at(bp == 0 ? n - 1 : bp - 1);
+        u = T.pred(b);
         v = b;
       }
       const int2 xu = T.coord(u), xv = T.coord(v);
       const int d_uv = euc2d(xu, xv);
       const int d_ua = euc2d(xu, xa), d_av = euc2d(xa, xv);
+      const bool base_bad = (u == p || v == p || u == a || v == a);
 #pragma unroll
       for (int l = 1; l <= 3; ++l) {
         const int q = l == 1 ? s1 : (l == 2 ? s2 : s3);
-        bool bad = (u == p || v == p || u == q || v == q || u == a || v == a);
+        bool bad = base_bad || u == q || v == q;
         if (l >= 2) bad |= (u == s1 || v == s1);
         if (l >= 3) bad |= (u == s2 || v == s2);
         if (bad) continue;
         const int64_t rem = l == 1 ? rem1 : (l == 2 ? rem2 : rem3);
-        const int2 xe = l == 1 ? xa : (l == 2 ? x1 : x2);
-        {  // reversed: u-e ... a-v
-          const int64_t g = rem + d_uv - euc2d(xu, xe) - d_av;
-          const int idx = (((l - 1) * k + s) * 2 + side) * 2 + 0;
+        if (l == 1) {  // one node: only the reversed form, u-a-v
+          const int64_t g = rem + d_uv - d_ua - d_av;
           if (g > lbest) {
             lbest = g;
-            lidx = idx;
+            lidx = ((s * 2 + side) * 2);
           }
-        }
-        if (l >= 2) {  // kept: u-a ... e-v
-          const int64_t g = rem + d_uv - d_ua - euc2d(xe, xv);
-          const int idx = (((l - 1) * k + s) * 2 + side) * 2 + 1;
-          if (g > lbest) {
-            lbest = g;
-            lidx = idx;
+        } else {
+          const int2 xe = l == 2 ? x1 : x2;
+          const int d_ue = euc2d(xu, xe), d_ev = euc2d(xe, xv);
+          const int base = (((l - 1) * k + s) * 2 + side) * 2;
+          const int64_t g0 = rem + d_uv - d_ue - d_av;  // reversed: u-e ... a-v
+          if (g0 > lbest) {
+            lbest = g0;
+            lidx = base;
+          }
+          const int64_t g1 = rem + d_uv - d_ua - d_ev;  // kept: u-a ... e-v
+          if (g1 > lbest) {
+            lbest = g1;
+            lidx = base + 1;
           }
         }
       }
@@ -257,15 +263,150 @@ __device__ __noinline__ int64_t eval_or(const Tour& T, int a, int mv[7]) {
     int u, v;
     if (side == 0) {
       u = b;
-      v = tour_succ(T, b);
+      v = T.succ(b);
     } else {
-      u = tour_pred(T, b);
+      u = T.pred(b);
       v = b;
     }
     mv[0] = p; mv[1] = a; mv[2] = l == 1 ? a : (l == 2 ? s1 : s2);
     mv[3] = l == 1 ? s1 : (l == 2 ? s2 : s3); mv[4] = u; mv[5] = v; mv[6] = kept;
   }
   return lbest;
+}
+
+// Both scans from a in one pass over NN(a) (one lookup of a, one of each
+// neighbour b): the best 2-opt move (as eval_2opt) and, when do_or, the best
+// Or-opt move (as eval_or).  The search then takes the 2-opt move if it
+// gains, else the Or-opt move -- the same decision as scanning one after the
+// other.
+template <class Tour>
+__device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int64_t& g2, int mv2[4],
+                                          int64_t& go, int mvo[7]) {
+  const int n = T.n, k = T.k, lane = lane_id();
+  do_or = do_or && n >= 8;
+  int p, s1, s2 = -1, s3 = -1;
+  if (do_or)
+    T.walk(a, p, s1, s2, s3);
+  else
+    T.nbrs(a, p, s1);
+  const int2 xa = T.coord(a), x1 = T.coord(s1), xp = T.coord(p);
+  const int d_as = euc2d(xa, x1), d_ap = euc2d(xp, xa);
+  int64_t rem1 = 0, rem2 = 0, rem3 = 0;
+  int2 x2 = xa, x3 = xa;
+  if (do_or) {
+    x2 = T.coord(s2);
+    x3 = T.coord(s3);
+    rem1 = (int64_t)d_ap + d_as - euc2d(xp, x1);
+    rem2 = (int64_t)d_ap + euc2d(x1, x2) - euc2d(xp, x2);
+    rem3 = (int64_t)d_ap + euc2d(x2, x3) - euc2d(xp, x3);
+  }
+  int64_t b2 = 0, bo = 0;
+  int i2 = INT_MAX, io = INT_MAX;
+  const int passes = k <= 16 ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int side = k <= 16 ? (lane >> 4) : pass;
+    const int s = k <= 16 ? (lane & 15) : lane;
+    int64_t g = 0;
+    int64_t lo = 0;
+    int li = INT_MAX;
+    if (s < k) {
+      const int b = T.cand(a, s);
+      const int bn = side == 0 ? T.succ(b) : T.pred(b);
+      const int2 xb = T.coord(b), xbn = T.coord(bn);
+      const int d_ab = euc2d(xa, xb);
+      const int d_bbn = euc2d(xb, xbn);
+      if (side == 0) {
+        if (d_as > d_ab) g = (int64_t)d_as + d_bbn - d_ab - euc2d(x1, xbn);
+      } else {
+        if (d_ap > d_ab) g = (int64_t)d_ap + d_bbn - d_ab - euc2d(xp, xbn);
+      }
+      if (do_or) {
+        // the tour edge (u, v) at b: (b, succ b) or (pred b, b)
+        const int u = side == 0 ? b : bn, v = side == 0 ? bn : b;
+        const int2 xu = side == 0 ? xb : xbn, xv = side == 0 ? xbn : xb;
+        const int d_uv = d_bbn;
+        const int d_ua = side == 0 ? d_ab : euc2d(xu, xa);
+        const int d_av = side == 0 ? euc2d(xa, xv) : d_ab;
+        const bool base_bad = (u == p || v == p || u == a || v == a);
+#pragma unroll
+        for (int l = 1; l <= 3; ++l) {
+          const int q = l == 1 ? s1 : (l == 2 ? s2 : s3);
+          bool bad = base_bad || u == q || v == q;
+          if (l >= 2) bad |= (u == s1 || v == s1);
+          if (l >= 3) bad |= (u == s2 || v == s2);
+          if (bad) continue;
+          const int64_t rem = l == 1 ? rem1 : (l == 2 ? rem2 : rem3);
+          if (l == 1) {  // one node: only the reversed form, u-a-v
+            const int64_t gg = rem + d_uv - d_ua - d_av;
+            if (gg > lo) {
+              lo = gg;
+              li = (s * 2 + side) * 2;
+            }
+          } else {
+            const int2 xe = l == 2 ? x1 : x2;
+            const int d_ue = euc2d(xu, xe), d_ev = euc2d(xe, xv);
+            const int base = (((l - 1) * k + s) * 2 + side) * 2;
+            const int64_t g0 = rem + d_uv - d_ue - d_av;  // reversed: u-e ... a-v
+            if (g0 > lo) {
+              lo = g0;
+              li = base;
+            }
+            const int64_t g1 = rem + d_uv - d_ua - d_ev;  // kept: u-a ... e-v
+            if (g1 > lo) {
+              lo = g1;
+              li = base + 1;
+            }
+          }
+        }
+      }
+    }
+    int idx = side * k + s;
+    if (!(g > 0)) {
+      g = 0;
+      idx = INT_MAX;
+    }
+    warp_max_gain(g, idx);
+    if (g > b2) {
+      b2 = g;
+      i2 = idx;
+    }
+    if (do_or) {
+      if (!(lo > 0)) {
+        lo = 0;
+        li = INT_MAX;
+      }
+      warp_max_gain(lo, li);
+      if (lo > bo || (lo == bo && lo > 0 && li < io)) {
+        bo = lo;
+        io = li;
+      }
+    }
+  }
+  g2 = b2;
+  go = bo;
+  if (b2 > 0) {
+    const int side = i2 / k, s = i2 % k;
+    const int b = T.cand(a, s);
+    if (side == 0) {
+      mv2[0] = a; mv2[1] = s1; mv2[2] = b; mv2[3] = T.succ(b);
+    } else {
+      mv2[0] = p; mv2[1] = a; mv2[2] = T.pred(b); mv2[3] = b;
+    }
+  } else if (bo > 0) {
+    const int kept = io & 1, side = (io >> 1) & 1, rest = io >> 2;
+    const int s = rest % k, l = rest / k + 1;
+    const int b = T.cand(a, s);
+    int u, v;
+    if (side == 0) {
+      u = b;
+      v = T.succ(b);
+    } else {
+      u = T.pred(b);
+      v = b;
+    }
+    mvo[0] = p; mvo[1] = a; mvo[2] = l == 1 ? a : (l == 2 ? s1 : s2);
+    mvo[3] = l == 1 ? s1 : (l == 2 ? s2 : s3); mvo[4] = u; mvo[5] = v; mvo[6] = kept;
+  }
 }
 
 // Applies an Or-opt move {p,a,e,q,u,v,kept} as edge exchanges.
@@ -293,8 +434,8 @@ __device__ __forceinline__ void ls_push0(const LsEnv& E, int x, int qh, int& qn)
 // Returns the total gain (old length - new length), or -1 if the tour
 // representation ran out of capacity (flags are left clean either way).
 template <class Tour>
-__device__ __noinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t* init, int ninit,
-                                       LsStats& S) {
+__device__ __forceinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t* init, int ninit,
+                                          LsStats& S) {
   const int n = E.n, lane = lane_id();
   for (int i = lane; i < ninit; i += 32) {
     const int x = init[i];
@@ -319,8 +460,9 @@ __device__ __noinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t* i
       if (!(f & 2)) ++nlog;
       __syncwarp();
       S.pops++;
-      int mv[7];
-      int64_t g = eval_2opt(T, a, mv);
+      int mv[4], mvo[7];
+      int64_t g, go;
+      eval_both(T, a, E.oropt != 0, g, mv, go, mvo);
       if (g > 0) {
         ok = T.flip(mv[1], mv[2], S);
         if (!ok) break;
@@ -335,12 +477,12 @@ __device__ __noinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t* i
         continue;
       }
       if (E.oropt) {
-        g = eval_or(T, a, mv);
+        g = go;
         if (g > 0) {
-          ok = apply_or(T, mv, S);
+          ok = apply_or(T, mvo, S);
           if (!ok) break;
           if (lane == 0)
-            for (int t = 0; t < 6; ++t) ls_push0(E, mv[t], qh, qn);
+            for (int t = 0; t < 6; ++t) ls_push0(E, mvo[t], qh, qn);
           qn = __shfl_sync(kFull, qn, 0);
           __syncwarp();
           total += g;
@@ -373,6 +515,146 @@ __device__ __noinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t* i
   for (int i = lane; i < nlog; i += 32) E.flags[E.logb[i]] = 0;
   __syncwarp();
   return ok ? total : -1;
+}
+
+// Shared scratch of the block version below.
+struct LsShared {
+  int64_t gain[32];
+  int mv[32][8];
+  int qh, qn, nlog, changes, moves_round, win, fail;
+  int64_t total;
+};
+
+// The same search run by a block of W warps on one tour: each round, warp w
+// evaluates the w-th queued node; entries are popped in queue order up to
+// and including the first one whose evaluation found a move, which warp 0
+// applies.  Nothing changes the tour between the confirmed evaluations, so
+// the result equals popping one node at a time.  Must be called by every
+// thread of the block.  Returns the gain, or -1 (capacity).
+template <class Tour>
+__device__ __forceinline__ int64_t ls_run_block(const LsEnv& E, Tour& T, const int32_t* init, int ninit,
+                                                LsStats& S, LsShared& sh) {
+  const int n = E.n, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int W = blockDim.x >> 5;
+  for (int i = tid; i < ninit; i += blockDim.x) {
+    const int x = init[i];
+    E.queue[i] = x;
+    E.flags[x] = 1;
+  }
+  if (tid == 0) {
+    sh.qh = 0; sh.qn = ninit; sh.nlog = 0; sh.changes = 0; sh.moves_round = 0; sh.fail = 0;
+    sh.total = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const int qh = sh.qh, qn = sh.qn;
+    if (qn == 0 || sh.changes >= n || sh.fail) {
+      if (sh.fail || sh.changes >= n || !E.verify || sh.moves_round == 0) break;
+      const int nl = sh.nlog;  // verify round: queue again the nodes popped
+      for (int i = tid; i < nl; i += blockDim.x) {
+        const int x = E.logb[i];
+        E.queue[i] = x;
+        E.flags[x] = 1;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        sh.qh = 0; sh.qn = nl; sh.nlog = 0; sh.moves_round = 0;
+      }
+      if (w == 0) S.verify++;
+      __syncthreads();
+      continue;
+    }
+    const int R = qn < W ? qn : W;
+    const uint64_t t0 = (w == 0) ? global_ns() : 0;
+    if (w < R) {
+      int idx = qh + w;
+      if (idx >= n) idx -= n;
+      const int a = E.queue[idx];
+      int mv2[4], mvo[7];
+      int64_t g2, go;
+      eval_both(T, a, E.oropt != 0, g2, mv2, go, mvo);
+      if (lane == 0) {
+        if (g2 > 0) {
+          sh.gain[w] = g2;
+          for (int t = 0; t < 4; ++t) sh.mv[w][t] = mv2[t];
+          sh.mv[w][7] = 0;
+        } else {
+          sh.gain[w] = go > 0 ? go : 0;
+          for (int t = 0; t < 7; ++t) sh.mv[w][t] = mvo[t];
+          sh.mv[w][7] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (w == 0) {
+      const uint64_t t1 = global_ns();
+      S.t_eval += (int64_t)(t1 - t0);
+      const unsigned bal = __ballot_sync(kFull, lane < R && sh.gain[lane] > 0);
+      const int first = bal ? __ffs(bal) - 1 : R;
+      const int cnt = bal ? first + 1 : R;  // queue entries popped this round
+      int a = -1;
+      bool first_pop = false;
+      if (lane < cnt) {
+        int idx = qh + lane;
+        if (idx >= n) idx -= n;
+        a = E.queue[idx];
+        const uint8_t f = E.flags[a];
+        first_pop = !(f & 2);
+        E.flags[a] = (uint8_t)((f & ~1) | 2);
+      }
+      const unsigned fb = __ballot_sync(kFull, first_pop);
+      if (first_pop) E.logb[sh.nlog + __popc(fb & ((1u << lane) - 1u))] = a;
+      S.pops += cnt;
+      __syncwarp();
+      int qh2 = qh + cnt;
+      if (qh2 >= n) qh2 -= n;
+      int qn2 = qn - cnt;
+      const uint64_t t2 = global_ns();
+      S.t_confirm += (int64_t)(t2 - t1);
+      if (bal) {  // apply the first move found, queue its endpoints
+        int mv[8];
+        for (int t = 0; t < 8; ++t) mv[t] = sh.mv[first][t];
+        bool ok;
+        if (mv[7] == 0) {
+          ok = T.flip(mv[1], mv[2], S);
+          S.moves2++;
+        } else {
+          ok = apply_or(T, mv, S);
+          S.movesor++;
+        }
+        const uint64_t t3 = global_ns();
+        S.t_flip += (int64_t)(t3 - t2);
+        if (!ok) {
+          if (lane == 0) sh.fail = 1;
+        } else if (lane == 0) {
+          const int np = mv[7] == 0 ? 4 : 6;
+          for (int t = 0; t < np; ++t) ls_push0(E, mv[t], qh2, qn2);
+          sh.total += sh.gain[first];
+          sh.changes++;
+          sh.moves_round++;
+        }
+        __syncwarp();
+        S.t_push += (int64_t)(global_ns() - t3);
+      }
+      if (lane == 0) {
+        sh.nlog += __popc(fb);
+        sh.qh = qh2;
+        sh.qn = qn2;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int qh = sh.qh, qn = sh.qn, nl = sh.nlog;
+  for (int t = tid; t < qn; t += blockDim.x) {
+    int i = qh + t;
+    if (i >= n) i -= n;
+    E.flags[E.queue[i]] = 0;
+  }
+  for (int i = tid; i < nl; i += blockDim.x) E.flags[E.logb[i]] = 0;
+  __syncthreads();
+  return sh.fail ? -1 : sh.total;
 }
 
 }  // namespace faco

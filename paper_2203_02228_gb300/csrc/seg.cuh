@@ -34,13 +34,14 @@ struct SegTab {
   int32_t* offA;     // [cap] sg[A[r]].off
   int32_t* loB;      // [cap] sg[B[r]].lo
   uint16_t* tmp;     // [2 * cap + 2] scratch
+  uint16_t* rankA;   // [cap] rank in A of each id
   int32_t* S;        // segment count (shared)
   int cap;
 };
 
 // bytes of shared memory per warp for a table of `cap` segments
 __host__ __device__ constexpr size_t segtab_bytes(int cap) {
-  return (size_t)cap * (sizeof(Seg) + 4 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 2 * sizeof(uint16_t) + 16;
+  return (size_t)cap * (sizeof(Seg) + 5 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 2 * sizeof(uint16_t) + 16;
 }
 
 __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
@@ -57,6 +58,8 @@ __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
   p += (size_t)cap * sizeof(uint16_t);
   T.tmp = reinterpret_cast<uint16_t*>(p);
   p += (size_t)(2 * cap + 2) * sizeof(uint16_t);
+  T.rankA = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * sizeof(uint16_t);
   T.S =reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
   T.cap = cap;
   return T;
@@ -107,7 +110,9 @@ __device__ __forceinline__ void u16_remove(uint16_t* arr, int S, int r) {
 __device__ __forceinline__ void segtab_keys(const SegTab& T) {
   const int S = *T.S;
   for (int r = lane_id(); r < S; r += 32) {
-    T.offA[r] = T.sg[T.A[r]].off;
+    const int ida = T.A[r];
+    T.offA[r] = T.sg[ida].off;
+    T.rankA[ida] = (uint16_t)r;
     T.loB[r] = T.sg[T.B[r]].lo;
   }
   __syncwarp();
@@ -118,8 +123,58 @@ __device__ __forceinline__ int rank_B(const SegTab& T, int id) {
   return bsearch_le(T.loB, *T.S, T.sg[id].lo);
 }
 
-// Ensure a segment starts at ant position t (0 < t < n).  Keys must be
-// current on entry and are current on exit.  false: table full.
+// Insert (id, key) at index r of the parallel arrays ids/keys[0..S)
+// (warp-collective); rank, when given, follows the moved ids.
+__device__ __forceinline__ void ins2(uint16_t* ids, int32_t* keys, uint16_t* rank, int S, int r, int id,
+                                     int32_t key) {
+  const int lane = lane_id();
+  for (int e = S - 1; e >= r; e -= 32) {
+    const int idx = e - lane;
+    uint16_t v = 0;
+    int32_t k = 0;
+    if (idx >= r) {
+      v = ids[idx];
+      k = keys[idx];
+    }
+    __syncwarp();
+    if (idx >= r) {
+      ids[idx + 1] = v;
+      keys[idx + 1] = k;
+      if (rank) rank[v] = (uint16_t)(idx + 1);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    ids[r] = (uint16_t)id;
+    keys[r] = key;
+    if (rank) rank[id] = (uint16_t)r;
+  }
+  __syncwarp();
+}
+
+// Remove index r of ids/keys[0..S) (warp-collective).
+__device__ __forceinline__ void del2(uint16_t* ids, int32_t* keys, uint16_t* rank, int S, int r) {
+  const int lane = lane_id();
+  for (int e = r + 1; e < S; e += 32) {
+    const int idx = e + lane;
+    uint16_t v = 0;
+    int32_t k = 0;
+    if (idx < S) {
+      v = ids[idx];
+      k = keys[idx];
+    }
+    __syncwarp();
+    if (idx < S) {
+      ids[idx - 1] = v;
+      keys[idx - 1] = k;
+      if (rank) rank[v] = (uint16_t)(idx - 1);
+    }
+    __syncwarp();
+  }
+}
+
+// Ensure a segment starts at ant position t (0 < t < n).  Keys are current
+// on entry and on exit.  false: table full.
 __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
   const int S = *T.S;
   const int r = bsearch_le(T.offA, S, t);
@@ -142,12 +197,53 @@ __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
     }
   }
   __syncwarp();
-  u16_insert(T.A, S, r + 1, (uint16_t)nid);
-  u16_insert(T.B, S, s.rev ? rb : rb + 1, (uint16_t)nid);
+  ins2(T.A, T.offA, T.rankA, S, r + 1, nid, t);
+  if (!s.rev) {
+    ins2(T.B, T.loB, nullptr, S, rb + 1, nid, s.lo + d);
+  } else {  // nid keeps the low end: it goes before id, whose lo moved up
+    ins2(T.B, T.loB, nullptr, S, rb, nid, s.lo);
+    if (lane_id() == 0) T.loB[rb + 1] = s.lo + s.len - d;
+  }
   if (lane_id() == 0) *T.S = S + 1;
   __syncwarp();
-  segtab_keys(T);
   return true;
+}
+
+// Merge ant ranks r and r+1 if the second continues the first in the
+// source (r + 1 > 0, so never across ant position 0).  Keys stay current.
+__device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
+  const int S = *T.S;
+  if (r < 0 || r + 1 >= S) return;
+  const int ia = T.A[r], ib = T.A[r + 1];
+  const Seg a = T.sg[ia], b = T.sg[ib];
+  if (!(a.rev == b.rev && (a.rev ? (b.lo + b.len == a.lo) : (a.lo + a.len == b.lo)))) return;
+  const int rbb = bsearch_le(T.loB, S, b.lo);
+  __syncwarp();
+  if (lane_id() == 0) {
+    T.sg[ia].len = a.len + b.len;
+    if (a.rev) T.sg[ia].lo = b.lo;
+  }
+  __syncwarp();
+  del2(T.A, T.offA, T.rankA, S, r + 1);
+  del2(T.B, T.loB, nullptr, S, rbb);
+  if (a.rev && lane_id() == 0) T.loB[rbb] = b.lo;  // a slid down to b's rank and took its lo
+  __syncwarp();
+  // free id ib: move the last id into its slot
+  const int last = S - 1;
+  if (ib != last) {
+    const Seg sl = T.sg[last];
+    const int ra = T.rankA[last];
+    const int rl = bsearch_le(T.loB, S - 1, sl.lo);
+    __syncwarp();
+    if (lane_id() == 0) {
+      T.sg[ib] = sl;
+      T.A[ra] = (uint16_t)ib;
+      T.rankA[ib] = (uint16_t)ra;
+      T.B[rl] = (uint16_t)ib;
+    }
+  }
+  if (lane_id() == 0) *T.S = S - 1;
+  __syncwarp();
 }
 
 // Drop id `dead` (already unlinked from A and B): move the last id into
@@ -228,6 +324,52 @@ struct SegTour {
   __device__ __forceinline__ int2 coord(int q) const { return xy[q]; }
   __device__ __forceinline__ int cand(int q, int s) const { return cn[(size_t)q * kw + s]; }
 
+  // Segment id holding source position q.
+  __device__ __forceinline__ int locate(int q) const { return T.B[bsearch_le(T.loB, *T.S, q)]; }
+  // Next / previous node in ant order from q (in segment id); id follows.
+  __device__ __forceinline__ int step_up(int q, int& id) const {
+    const Seg s = T.sg[id];
+    const int d = s.rev ? s.lo + s.len - 1 - q : q - s.lo;
+    if (d < s.len - 1) return s.rev ? q - 1 : q + 1;
+    int r = T.rankA[id] + 1;
+    if (r == *T.S) r = 0;
+    id = T.A[r];
+    const Seg t = T.sg[id];
+    return t.rev ? t.lo + t.len - 1 : t.lo;
+  }
+  __device__ __forceinline__ int step_dn(int q, int& id) const {
+    const Seg s = T.sg[id];
+    const int d = s.rev ? s.lo + s.len - 1 - q : q - s.lo;
+    if (d > 0) return s.rev ? q + 1 : q - 1;
+    int r = T.rankA[id] - 1;
+    if (r < 0) r = *T.S - 1;
+    id = T.A[r];
+    const Seg t = T.sg[id];
+    return t.rev ? t.lo : t.lo + t.len - 1;
+  }
+  __device__ __forceinline__ int succ(int q) const {
+    int id = locate(q);
+    return step_up(q, id);
+  }
+  __device__ __forceinline__ int pred(int q) const {
+    int id = locate(q);
+    return step_dn(q, id);
+  }
+  __device__ __forceinline__ void nbrs(int q, int& p, int& s) const {
+    const int id = locate(q);
+    int i1 = id, i2 = id;
+    p = step_dn(q, i1);
+    s = step_up(q, i2);
+  }
+  __device__ __forceinline__ void walk(int a, int& p, int& s1, int& s2, int& s3) const {
+    const int id = locate(a);
+    int i1 = id, i2 = id;
+    p = step_dn(a, i1);
+    s1 = step_up(a, i2);
+    s2 = step_up(s1, i2);
+    s3 = step_up(s2, i2);
+  }
+
   // Reverse the forward span x..y, or its complement when longer than n/2
   // (the array rule, entry for entry).  false: the table is full.
   __device__ __noinline__ bool flip(int x, int y, LsStats& St) {
@@ -266,7 +408,15 @@ struct SegTour {
         T.A[rj - m] = a;
       }
       __syncwarp();
-      segtab_keys(T);
+      for (int m = lane; m < c; m += 32) {  // keys of the reversed ranks
+        const int id = T.A[ri + m];
+        T.offA[ri + m] = T.sg[id].off;
+        T.rankA[id] = (uint16_t)(ri + m);
+      }
+      __syncwarp();
+      seg_merge_at(T, rj);      // the span's right end and its old right neighbour
+      seg_merge_at(T, ri - 1);  // its left neighbour and the span's new left end
+      return true;
     } else {
       // the span wraps: ranks ri..S-1 then 0..rj; lay the reversed list
       // out from position i, cutting the segment that crosses position 0

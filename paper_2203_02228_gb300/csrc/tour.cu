@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "ls.cuh"
+#include "nearest.cuh"
 
 namespace faco {
 
@@ -18,7 +19,8 @@ namespace {
 
 __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int32_t* cand, int k,
                                                 const int32_t* backup, int bl, int32_t* route,
-                                                uint32_t* vis_g) {
+                                                uint32_t* vis_g, Grid g, const int32_t* cstart,
+                                                const int32_t* cpts) {
   extern __shared__ uint32_t sv[];
   uint32_t* vis = vis_g ? vis_g : sv;
   const int lane = lane_id();
@@ -47,7 +49,13 @@ __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int
       if (bal) v = __shfl_sync(kFull, c, __ffs(bal) - 1);
     }
     if (v < 0) {
-      // global nearest unvisited node: scan visited words, skip full ones
+      // global nearest unvisited node: rings of grid cells, else a scan of
+      // the visited words that skips full ones
+      const int2 xu = xy[u];
+      v = ring_nearest(xy, g, cstart, cpts, xu, 24,
+                       [&](int x) { return ((vis[x >> 5] >> (x & 31)) & 1u) != 0; });
+    }
+    if (v < 0) {
       const int2 xu = xy[u];
       uint64_t bk = ~0ull;
       int32_t bi = INT_MAX;
@@ -108,7 +116,7 @@ __device__ void cta_flip(ArrTour& T, int x, int y) {
 }
 
 __device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4) {
-  const bool fwd = tour_succ(T, n1) == n2;
+  const bool fwd = T.succ(n1) == n2;
   if (fwd)
     cta_flip(T, n2, n3);
   else
@@ -161,17 +169,19 @@ __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const i
       int idx = qh + w;
       if (idx >= n) idx -= n;
       const int a = queue[idx];
-      int mv[7];
-      int64_t g = eval_2opt(T, a, mv);
-      int type = 0;
-      if (!(g > 0) && oropt) {
-        g = eval_or(T, a, mv);
-        type = 1;
-      }
+      int mv2[4], mvo[7];
+      int64_t g2, go;
+      eval_both(T, a, oropt != 0, g2, mv2, go, mvo);
       if (lane == 0) {
-        s_gain[w] = g > 0 ? g : 0;
-        for (int t = 0; t < 7; ++t) s_mv[w][t] = mv[t];
-        s_mv[w][7] = type;
+        if (g2 > 0) {
+          s_gain[w] = g2;
+          for (int t = 0; t < 4; ++t) s_mv[w][t] = mv2[t];
+          s_mv[w][7] = 0;
+        } else {
+          s_gain[w] = go > 0 ? go : 0;
+          for (int t = 0; t < 7; ++t) s_mv[w][t] = mvo[t];
+          s_mv[w][7] = 1;
+        }
       }
     }
     __syncthreads();
@@ -265,13 +275,14 @@ __global__ void k_tests(int what, const void* in, void* out, int count, int widt
 }  // namespace
 
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
-                           int bl, int32_t* route, uint32_t* vis_g, cudaStream_t s) {
+                           int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
+                           const int32_t* cpts, cudaStream_t s) {
   const size_t smem = vis_g ? 0 : (size_t)((n + 31) >> 5) * sizeof(uint32_t);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_nn_tour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g);
+  k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g, g, cstart, cpts);
   return cudaGetLastError();
 }
 
