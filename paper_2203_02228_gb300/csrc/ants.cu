@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
     if (lane == 0) A.nseg[ant] = Sn;
     if (A.keep_tours) seg_materialize(C, W.tab, route);
   } else {
-    ArrTour T{n, C.k, route, pos, C.xy, C.cand};
+    ArrTour T{n, C.k, route, pos, C.xy, C.cand, C.k};
     gain = ls_run(E, T, chk, W.nchk, S);
     if (lane == 0 && A.nseg) A.nseg[ant] = -1;  // tour is in route/pos
   }
@@ -554,6 +554,10 @@ __global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
 // speculative in-order pops (ls_run_block).  An ant whose table fills up is
 // marked and redone by the array kernel.
 constexpr int kAntWarps = 4;
+
+__device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
+  A.stats[(size_t)ant * kNStats + kStRedo] += 1;
+}
 
 template <int KW>
 __global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
@@ -609,21 +613,32 @@ __global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A
   LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
           A.logb + (size_t)ant * n};
   LsStats S{0, 0, 0, 0, 0};
-  SegTour T{n, C.k, C.kw, tab, C.XYsrc, C.Csrc};
+  __shared__ int32_t s_mode;
+  if (tid == 0) s_mode = 0;
+  __syncthreads();
+  HybTour T{n, C.k, SegTour{n, C.k, C.kw, tab, C.XYsrc, C.Csrc},
+            ArrTour{n, C.k, route, A.pos + (size_t)ant * n, C.XYsrc, C.Csrc, C.kw}, &s_mode};
   const int64_t gain = ls_run_block(E, T, chk, s_nchk, S, sh);
-  if (gain < 0) {  // the table filled up during the search
-    if (tid == 0) A.redo[ant] = 1;
-    return;
+  // hand the tour over: segments in ant order, or arrays of source positions
+  // (-2) when the table filled up; arrays of node ids (-1) for inspection
+  int Sn;
+  if (!s_mode) {
+    Sn = *tab.S;
+    int4* out = A.segs + (size_t)ant * A.seg_cap;
+    for (int r = tid; r < Sn; r += blockDim.x) {
+      const Seg s = tab.sg[tab.A[r]];
+      out[r] = make_int4(s.lo, s.len, s.off, s.rev);
+    }
+    if (w == 0 && A.keep_tours) seg_materialize(C, tab, route);
+  } else {
+    Sn = -2;
+    if (A.keep_tours) {
+      Sn = -1;
+      for (int t = tid; t < n; t += blockDim.x) route[t] = C.src_route[route[t]];
+    }
   }
-  // hand the tour over: segments in ant order
-  const int Sn = *tab.S;
-  int4* out = A.segs + (size_t)ant * A.seg_cap;
-  for (int r = tid; r < Sn; r += blockDim.x) {
-    const Seg s = tab.sg[tab.A[r]];
-    out[r] = make_int4(s.lo, s.len, s.off, s.rev);
-  }
-  if (w == 0 && A.keep_tours) seg_materialize(C, tab, route);
   if (tid == 0) {
+    if (s_mode) st_redo_add(A, ant);
     A.nseg[ant] = Sn;
     A.len[ant] = s_pre_len - gain;
     A.redo[ant] = 0;

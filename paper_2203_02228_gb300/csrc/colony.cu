@@ -164,8 +164,10 @@ __global__ void k_best_tour(Colony C, Ants A, int32_t* tmp_route, int32_t* tmp_p
   const int a = st->it_best_ant;
   int node;
   const int S = A.nseg ? A.nseg[a] : -1;
-  if (S < 0) {
+  if (S == -1) {  // node ids
     node = A.route[(size_t)a * n + t];
+  } else if (S < 0) {  // source positions
+    node = C.src_route[A.route[(size_t)a * n + t]];
   } else {
     const int4* sg = A.segs + (size_t)a * A.seg_cap;
     int lo = 0, hi = S - 1;

@@ -48,13 +48,16 @@ struct LsStats {
   int64_t t_eval, t_confirm, t_flip, t_push;  // device ns per phase (block search)
 };
 
-// Explicit tour: route[t] = node at position t, pos = inverse.
+// Explicit tour: route[t] = node at position t, pos = inverse.  Nodes are
+// node ids (with node-indexed xy/cn) or source positions (with the
+// source-ordered copies); cn rows are `stride` entries apart.
 struct ArrTour {
   int n, k;
   int32_t* route;
   int32_t* pos;
-  const int2* xy;       // node-indexed coordinates
-  const int32_t* cn;    // node-indexed candidate lists [n][k]
+  const int2* xy;       // coordinates by node
+  const int32_t* cn;    // candidate lists by node [n][stride]
+  int stride;
   __device__ __forceinline__ int pos_of(int x) const { return pos[x]; }
   __device__ __forceinline__ int at_off(int p, int d) const {
     p += d;
@@ -77,7 +80,7 @@ struct ArrTour {
     s3 = at_off(t, 3);
   }
   __device__ __forceinline__ int2 coord(int x) const { return xy[x]; }
-  __device__ __forceinline__ int cand(int x, int s) const { return cn[(size_t)x * k + s]; }
+  __device__ __forceinline__ int cand(int x, int s) const { return cn[(size_t)x * stride + s]; }
 
   // Reverse the forward span x..y (or its complement when longer than n/2).
   __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {

@@ -385,8 +385,14 @@ struct SegTour {
       j = j2;
       L = n - L;
     }
+    if (L <= 1) {
+      St.flip += L;
+      return true;
+    }
+    // a reversal adds at most three segments (two cuts, one at position 0):
+    // refuse before touching the table, which then still holds the tour
+    if (*T.S + 3 > T.cap) return false;
     St.flip += L;
-    if (L <= 1) return true;
     const int j1 = (j + 1 == n) ? 0 : j + 1;
     if (i != 0 && !seg_split(T, i)) return false;
     if (j1 != 0 && !seg_split(T, j1)) return false;
@@ -504,6 +510,60 @@ struct SegTour {
     }
     seg_merge_all(T);
     return true;
+  }
+};
+
+// A segment tour that moves to explicit arrays the first time its table is
+// full: the table (which still holds the tour) is written out as
+// route[t] = source position, pos = inverse, and the search goes on there
+// with the same node names, queue and counters.
+struct HybTour {
+  int n, k;
+  SegTour sg;
+  ArrTour ar;       // over source positions (XYsrc, Csrc), used once *mode != 0
+  int32_t* mode;    // shared flag: 0 = table, 1 = arrays
+
+  __device__ __forceinline__ bool arrays() const { return *mode != 0; }
+  __device__ __forceinline__ int pos_of(int x) const { return arrays() ? ar.pos_of(x) : sg.pos_of(x); }
+  __device__ __forceinline__ int succ(int x) const { return arrays() ? ar.succ(x) : sg.succ(x); }
+  __device__ __forceinline__ int pred(int x) const { return arrays() ? ar.pred(x) : sg.pred(x); }
+  __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
+    if (arrays())
+      ar.nbrs(x, p, s);
+    else
+      sg.nbrs(x, p, s);
+  }
+  __device__ __forceinline__ void walk(int a, int& p, int& s1, int& s2, int& s3) const {
+    if (arrays())
+      ar.walk(a, p, s1, s2, s3);
+    else
+      sg.walk(a, p, s1, s2, s3);
+  }
+  __device__ __forceinline__ int2 coord(int x) const { return sg.coord(x); }
+  __device__ __forceinline__ int cand(int x, int s) const { return sg.cand(x, s); }
+
+  __device__ __noinline__ void to_arrays() {
+    const int S = *sg.T.S;
+    for (int r = 0; r < S; ++r) {
+      const Seg s = sg.T.sg[sg.T.A[r]];
+      for (int d = lane_id(); d < s.len; d += 32) {
+        const int q = s.rev ? s.lo + s.len - 1 - d : s.lo + d;
+        ar.route[s.off + d] = q;
+        ar.pos[q] = s.off + d;
+      }
+    }
+    __syncwarp();
+    if (lane_id() == 0) *mode = 1;
+    __syncwarp();
+  }
+
+  // warp-collective; never fails
+  __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {
+    if (!arrays()) {
+      if (sg.flip(x, y, S)) return true;
+      to_arrays();
+    }
+    return ar.flip(x, y, S);
   }
 };
 

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const i
   __shared__ int s_mv[32][8];
   __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win;
   LsEnv E{n, oropt, verify, queue, flags, logb};
-  ArrTour T{n, k, route, pos, xy, cand};
+  ArrTour T{n, k, route, pos, xy, cand, k};
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   for (int i = tid; i < n; i += blockDim.x) {
     const int x = route[i];
