@@ -190,6 +190,31 @@ int faco_get_ant_pre(faco_ctx* c, int32_t* tours, int64_t* lens, int32_t* checkl
  * pop confirmation, move application, endpoint queueing.  19-23: zero. */
 int faco_get_ant_stats(faco_ctx* c, int64_t* stats);
 
+/* ---- candidate lists without device allocation --------------------------
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not let a library allocate device memory -- applications whose memory
+ * manager owns the whole device (a fixed pool in a serving process, a
+ * framework's caching allocator), or loops that cannot afford the device
+ * synchronisation that cudaMalloc/cudaFree imply.
+ *
+ * Builds the same candidate lists, backup lists and eta = 1/d as
+ * faco_create (k + bl nearest other nodes by exact distance, ties by index)
+ * for n device-resident (x, y) pairs, into caller-owned device buffers:
+ * cand_dev and eta_dev with n * k' entries, backup_dev with n * bl' entries
+ * (k' = min(k, n-1), bl' = min(bl, n-1-k'); backup_dev may be NULL when
+ * bl' = 0).  It calls no allocating routine: its scratch (the point grid)
+ * is a fixed array inside the library, reserved on every GPU that loads
+ * the library until the process exits; n may be at most 262144
+ * (FACO_E_SIZE above).  The first call on a device looks up that array's
+ * device address, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The call
+ * synchronises `stream` (a cudaStream_t, NULL = legacy default stream)
+ * once, to size the grid.  Errors: FACO_E_ARG (sizes, NULL buffers,
+ * coordinates outside [0, 2^24)), FACO_E_SIZE (n > 262144), FACO_E_CUDA. */
+int faco_lists_noalloc(const int32_t* coords_dev, int32_t n, int32_t k, int32_t bl, int32_t* cand_dev,
+                       int32_t* backup_dev, float* eta_dev, void* stream);
+
 /* ---- device self-test hook (used by the test-suite) ----------------------
  * Runs one of the library's device primitives on `count` inputs copied from
  * host memory and copies the results back (synchronous, default stream):

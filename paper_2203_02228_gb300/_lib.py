@@ -111,6 +111,7 @@ def load():
             "faco_get_ant_tours": (ctypes.c_int, [vp, vp, vp]),
             "faco_get_ant_pre": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "faco_get_ant_stats": (ctypes.c_int, [vp, vp]),
+            "faco_lists_noalloc": (ctypes.c_int, [vp, i32, i32, i32, vp, vp, vp, vp]),
             "faco_profile_enable":(ctypes.c_int, [vp, ctypes.c_int]),
             "faco_profile_read": (ctypes.c_int, [vp, P(ctypes.c_double), P(i64)]),
             "faco_test_device":(ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_size_t,
