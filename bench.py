@@ -113,6 +113,35 @@ def host_cores() -> int:
     return os.cpu_count() or 1
 
 
+# Sources of the per-ant kernel; the DRAM traffic recorded under profiles/
+# applies only while their hash matches the one recorded with it.
+ANTS_SOURCES = ["ants.cu", "ls.cuh", "seg.cuh", "nearest.cuh", "common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_ants_blk_stippled100k_traffic.json")
+
+
+def ants_sources_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ANTS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_02228_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the per-ant kernel from one ncu capture, or
+    None when the kernel changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        if rec.get("sources_sha256") == ants_sources_hash():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def oracle_sample(xy, ants, iters, k, sample_ants, sample_iters, threads):
     """Times the oracle's set-up and `sample_iters` iterations of
     `sample_ants` ants; returns the full-job throughput implied by them."""
@@ -286,9 +315,9 @@ def main():
 
     peak, peak_src = load_peaks()
     achieved = (algo_bytes / ants_launches) / (ants_ms / ants_launches / 1e3) / 1e9 if ants_launches else None
-    roofline = {"kernel": "k_ants (construction + local search)", "bound": "hbm", "achieved": achieved,
+    roofline = {"kernel": "k_ants_blk (construction + local search)", "bound": "hbm", "achieved": achieved,
                 "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
                 "avg_launch_ms": ants_ms / ants_launches if ants_launches else None,
                 "algorithmic_bytes_per_launch": algo_bytes / ants_launches if ants_launches else None}
 

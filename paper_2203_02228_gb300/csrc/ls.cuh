@@ -421,6 +421,30 @@ __device__ __forceinline__ bool apply_or(Tour& T, const int mv[7], LsStats& S) {
   return true;
 }
 
+// Queue the np (<= 32) nodes x[0..np) in order, each only if it is not
+// queued yet (and not already pushed earlier in the list): lane t handles
+// x[t].  Warp-collective; every lane receives the new qn.
+__device__ __forceinline__ int ls_push_warp(const LsEnv& E, const int* x, int np, int qh, int qn) {
+  const int lane = lane_id();
+  int node = -1 - lane;  // distinct dummies for idle lanes
+  if (lane < np) node = x[lane];
+  const unsigned same = __match_any_sync(kFull, node);
+  const bool leader = (same & ((1u << lane) - 1u)) == 0;  // first lane with this node
+  uint8_t f = 0;
+  if (lane < np && leader) f = E.flags[node];
+  const bool push = lane < np && leader && !(f & 1);
+  const unsigned bal = __ballot_sync(kFull, push);
+  if (push) {
+    E.flags[node] = f | 1;
+    int t = qh + qn + __popc(bal & ((1u << lane) - 1u));
+    if (t >= E.n) t -= E.n;
+    if (t >= E.n) t -= E.n;
+    E.queue[t] = node;
+  }
+  __syncwarp();
+  return qn + __popc(bal);
+}
+
 // FIFO push by lane 0 (the caller broadcasts qn afterwards).
 __device__ __forceinline__ void ls_push0(const LsEnv& E, int x, int qh, int& qn) {
   const uint8_t f = E.flags[x];
@@ -469,10 +493,7 @@ __device__ __forceinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t
       if (g > 0) {
         ok = T.flip(mv[1], mv[2], S);
         if (!ok) break;
-        if (lane == 0)
-          for (int t = 0; t < 4; ++t) ls_push0(E, mv[t], qh, qn);
-        qn = __shfl_sync(kFull, qn, 0);
-        __syncwarp();
+        qn = ls_push_warp(E, mv, 4, qh, qn);
         total += g;
         ++changes;
         ++moves_round;
@@ -484,10 +505,7 @@ __device__ __forceinline__ int64_t ls_run(const LsEnv& E, Tour& T, const int32_t
         if (g > 0) {
           ok = apply_or(T, mvo, S);
           if (!ok) break;
-          if (lane == 0)
-            for (int t = 0; t < 6; ++t) ls_push0(E, mvo[t], qh, qn);
-          qn = __shfl_sync(kFull, qn, 0);
-          __syncwarp();
+          qn = ls_push_warp(E, mvo, 6, qh, qn);
           total += g;
           ++changes;
           ++moves_round;
@@ -629,12 +647,13 @@ __device__ __forceinline__ int64_t ls_run_block(const LsEnv& E, Tour& T, const i
         S.t_flip += (int64_t)(t3 - t2);
         if (!ok) {
           if (lane == 0) sh.fail = 1;
-        } else if (lane == 0) {
-          const int np = mv[7] == 0 ? 4 : 6;
-          for (int t = 0; t < np; ++t) ls_push0(E, mv[t], qh2, qn2);
-          sh.total += sh.gain[first];
-          sh.changes++;
-          sh.moves_round++;
+        } else {
+          qn2 = ls_push_warp(E, mv, mv[7] == 0 ? 4 : 6, qh2, qn2);
+          if (lane == 0) {
+            sh.total += sh.gain[first];
+            sh.changes++;
+            sh.moves_round++;
+          }
         }
         __syncwarp();
         S.t_push += (int64_t)(global_ns() - t3);

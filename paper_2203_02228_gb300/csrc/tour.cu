@@ -223,13 +223,13 @@ __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const i
         cta_move2(T, mv[0], mv[4], mv[3], mv[2]);
         if (mv[6]) cta_move2(T, mv[4], mv[2], mv[1], mv[5]);
       }
-      if (tid == 0) {
-        int qn2 = s_qn;
-        const int np = mv[7] == 0 ? 4 : 6;
-        for (int t = 0; t < np; ++t) ls_push0(E, mv[t], s_qh, qn2);
-        s_qn = qn2;
-        s_changes++;
-        s_moves_round++;
+      if (w == 0) {
+        const int qn2 = ls_push_warp(E, mv, mv[7] == 0 ? 4 : 6, s_qh, s_qn);
+        if (lane == 0) {
+          s_qn = qn2;
+          s_changes++;
+          s_moves_round++;
+        }
       }
       __syncthreads();
     }
