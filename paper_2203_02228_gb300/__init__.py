@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib
 from ._lib import FacoError, faco_params, faco_stats, load, params_default  # noqa: F401
 
-__all__ = ["Colony", "FacoError", "faco_params", "faco_stats", "load", "params_default",
+__all__ = ["Batch", "Colony", "FacoError", "faco_params", "faco_stats", "load", "params_default",
            "faco_create", "faco_create_ex", "faco_create_device", "faco_iterate", "faco_sync",
            "faco_best", "faco_best_device", "faco_stats_get", "faco_destroy", "faco_strerror"]
 
@@ -216,6 +216,102 @@ class Colony:
         _lib.check(self._L.faco_get_ant_pre(self._h, _ptr(t), _ptr(lens), _ptr(chk), _ptr(nchk)),
                    "faco_get_ant_pre")
         return t, lens, [chk[i, :nchk[i]].copy() for i in range(m)]
+
+
+class Batch:
+    """Independent colonies run through the same launches (include/faco_batch.h).
+
+    Colony i equals ``Colony(coords[i], k, params with seed=seeds[i])`` driven by
+    the same ``iterate`` calls, bit for bit; the batch only shares the GPU.
+    """
+
+    def __init__(self, coords_list, k: int = 16, params: faco_params | None = None, seeds=None,
+                 stream=None, plan: int | None = None, **kw):
+        p = params if params is not None else params_default()
+        for key, v in kw.items():
+            setattr(p, key, v)
+        if stream is not None:
+            p.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.params = p
+        self._L = load()
+        self._coords = [np.ascontiguousarray(c, dtype=np.int32).reshape(-1, 2) for c in coords_list]
+        self.count = len(self._coords)
+        self.ns = np.array([c.shape[0] for c in self._coords], dtype=np.int32)
+        ptrs = (ctypes.c_void_p * self.count)(*[c.ctypes.data for c in self._coords])
+        sd = None
+        if seeds is not None:
+            self._seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+            assert self._seeds.shape[0] == self.count
+            sd = self._seeds.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        _lib.check(self._L.faco_batch_create(ctypes.cast(ptrs, ctypes.c_void_p), _ptr(self.ns), self.count, k,
+                                             ctypes.byref(p), sd, ctypes.byref(h)), "faco_batch_create")
+        self._h = h
+        self._coords = None  # copied by the library
+        if plan is not None:
+            self.set_plan(plan)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.faco_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def iterate(self, ants: int, budget: int = 1) -> None:
+        _lib.check(self._L.faco_batch_iterate(self._h, ants, budget), "faco_batch_iterate")
+
+    def sync(self) -> None:
+        _lib.check(self._L.faco_batch_sync(self._h), "faco_batch_sync")
+
+    def best(self, i: int):
+        tour = np.empty(int(self.ns[i]), np.int32)
+        L = ctypes.c_int64()
+        _lib.check(self._L.faco_batch_best(self._h, i, _ptr(tour), tour.shape[0], ctypes.byref(L)),
+                   "faco_batch_best")
+        return tour, int(L.value)
+
+    def tours(self):
+        """All global-best tours (list of arrays) and lengths."""
+        flat = np.empty(int(self.ns.sum()), np.int32)
+        lens = np.empty(self.count, np.int64)
+        _lib.check(self._L.faco_batch_tours(self._h, _ptr(flat), _ptr(lens)), "faco_batch_tours")
+        off = np.concatenate([[0], np.cumsum(self.ns)])
+        return [flat[off[i]:off[i + 1]] for i in range(self.count)], lens
+
+    def lengths(self) -> np.ndarray:
+        lens = np.empty(self.count, np.int64)
+        _lib.check(self._L.faco_batch_tours(self._h, None, _ptr(lens)), "faco_batch_tours")
+        return lens
+
+    def stats(self, i: int) -> faco_stats:
+        s = faco_stats()
+        _lib.check(self._L.faco_batch_stats(self._h, i, ctypes.byref(s)), "faco_batch_stats")
+        return s
+
+    def tau(self, i: int) -> np.ndarray:
+        st = self.stats(i)
+        t = np.empty((st.n, st.k), np.float32)
+        _lib.check(self._L.faco_batch_tau(self._h, i, _ptr(t)), "faco_batch_tau")
+        return t
+
+    def set_plan(self, mode: int) -> None:
+        _lib.check(self._L.faco_batch_set_plan(self._h, mode), "faco_batch_set_plan")
+
+    def plan(self) -> np.ndarray:
+        v = np.empty(self.count, np.int32)
+        _lib.check(self._L.faco_batch_get_plan(self._h, _ptr(v)), "faco_batch_get_plan")
+        return v
 
 
 def device_selftest(what: int, inp: np.ndarray, out: np.ndarray, count: int, width: int = 16, seed: int = 0) -> None:

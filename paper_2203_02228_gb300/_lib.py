@@ -116,6 +116,17 @@ def load():
             "faco_profile_read": (ctypes.c_int, [vp, P(ctypes.c_double), P(i64)]),
             "faco_test_device":(ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_size_t,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+            # include/faco_batch.h
+            "faco_batch_create": (ctypes.c_int, [vp, vp, i32, i32, P(faco_params), vp, P(vp)]),
+            "faco_batch_iterate": (ctypes.c_int, [vp, i32, i32]),
+            "faco_batch_sync": (ctypes.c_int, [vp]),
+            "faco_batch_best": (ctypes.c_int, [vp, i32, vp, i32, P(i64)]),
+            "faco_batch_tours": (ctypes.c_int, [vp, vp, vp]),
+            "faco_batch_stats": (ctypes.c_int, [vp, i32, P(faco_stats)]),
+            "faco_batch_tau": (ctypes.c_int, [vp, i32, vp]),
+            "faco_batch_set_plan": (ctypes.c_int, [vp, i32]),
+            "faco_batch_get_plan": (ctypes.c_int, [vp, vp]),
+            "faco_batch_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -459,18 +459,17 @@ __device__ void seg_finish_construction(const SegTab& T) {
   segtab_keys(T);
 }
 
+// Array kernel body: one warp runs ant `ant` with explicit route/pos;
+// `mine` is the warp's own shared memory (visited bits, and the segment
+// table when SEGS).
 template <int KW, bool SEGS>
-__global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
-  extern __shared__ __align__(16) char smem[];
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
-  const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
+__device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, int ant, char* mine) {
+  const int lane = lane_id();
   if (ant >= A.m) return;
   if (!SEGS && A.redo && !A.redo[ant]) return;  // array kernel: only the ants the table could not hold
   const int n = C.n;
   const int words = (n + 31) >> 5;
   const size_t vis_bytes = ((size_t)words * 4 + 15) & ~(size_t)15;
-  const size_t per_warp = SEGS ? vis_bytes + segtab_bytes(A.seg_cap) : (A.smem_vis ? vis_bytes : 0);
-  char* mine = smem + (size_t)wib * per_warp;
   uint32_t* vis = (SEGS || A.smem_vis) ? reinterpret_cast<uint32_t*>(mine) : A.vis_g + (size_t)ant * words;
   const uint32_t iter = (uint32_t)(C.st->iter + 1);
   const uint64_t t_start = global_ns();
@@ -559,14 +558,15 @@ __device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
   A.stats[(size_t)ant * kNStats + kStRedo] += 1;
 }
 
+// Segment-table kernel body: the whole block runs ant `ant`.  Returns true
+// (in every thread) when the table filled up during construction and the
+// ant is left to the array kernel.
 template <int KW>
-__global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
+__device__ __forceinline__ bool ants_blk_body(const Colony& C, const Ants& A, int ant) {
   extern __shared__ __align__(16) char smem[];
   __shared__ LsShared sh;
   __shared__ int s_nchk, s_overflow;
   __shared__ int64_t s_pre_len;
-  const int ant = blockIdx.x;
-  if (ant >= A.m) return;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int n = C.n;
   const int words = (n + 31) >> 5;
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A
   __syncthreads();
   if (s_overflow) {
     if (tid == 0) A.redo[ant] = 1;
-    return;
+    return true;
   }
   LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
           A.logb + (size_t)ant * n};
@@ -657,6 +657,83 @@ __global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A
     st[kStFlipNs] = S.t_flip;
     st[kStPushNs] = S.t_push;
   }
+  return false;
+}
+
+// ---------------------------------------------------------------------
+// Kernels.  One colony: the Colony and Ants descriptors are kernel
+// parameters.  A batch of colonies: every block reads its (colony, ant)
+// from a block map and the colony's descriptors from device tables into
+// shared memory; the bodies are the same.
+// ---------------------------------------------------------------------
+template <int KW, bool SEGS>
+__global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
+  extern __shared__ __align__(16) char smem[];
+  const int wib = threadIdx.x >> 5;
+  const int ant = blockIdx.x * (blockDim.x >> 5) + wib;
+  const size_t vis_bytes = ((size_t)((C.n + 31) >> 5) * 4 + 15) & ~(size_t)15;
+  const size_t per_warp = SEGS ? vis_bytes + segtab_bytes(A.seg_cap) : (A.smem_vis ? vis_bytes : 0);
+  ants_arr_body<KW, SEGS>(C, A, ant, smem + (size_t)wib * per_warp);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
+  if ((int)blockIdx.x >= A.m) return;
+  (void)ants_blk_body<KW>(C, A, blockIdx.x);
+}
+
+// Copies `bytes` (a multiple of 4) with the threads lo..lo+cnt-1.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, size_t bytes, int lo, int cnt) {
+  const int nw = (int)(bytes >> 2);
+  for (int i = (int)threadIdx.x - lo; i < nw; i += cnt)
+    static_cast<int32_t*>(dst)[i] = static_cast<const int32_t*>(src)[i];
+}
+
+// Batch: block b runs ant map[b].y of colony map[b].x; an ant whose table
+// filled up is appended to the redo list.
+template <int KW>
+__global__ void __launch_bounds__(32 * kAntWarps, 7)
+    k_ants_blk_b(const Colony* cols, const Ants* ants, const int2* map, int2* redo_list, int32_t* redo_n) {
+  __shared__ Colony sC;
+  __shared__ Ants sA;
+  const int2 e = map[blockIdx.x];
+  copy_words(&sC, cols + e.x, sizeof(Colony), 0, blockDim.x);
+  copy_words(&sA, ants + e.x, sizeof(Ants), 0, blockDim.x);
+  __syncthreads();
+  if (e.y >= sA.m) return;
+  const bool over = ants_blk_body<KW>(sC, sA, e.y);
+  if (over && threadIdx.x == 0) redo_list[atomicAdd(redo_n, 1)] = e;
+}
+
+// Batch, arrays: blocks below nmap run the four ants map[b].y + warp of
+// colony map[b].x; the remaining blocks run the redo list, one entry per
+// warp in turn.  per_warp is the shared-memory stride of a warp.
+template <int KW>
+__global__ void __launch_bounds__(128, 1)
+    k_ants_b(const Colony* cols, const Ants* ants, const int2* map, int nmap, const int2* redo_list,
+             const int32_t* redo_n, size_t per_warp) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ Colony sC[4];
+  __shared__ Ants sA[4];
+  const int wib = threadIdx.x >> 5;
+  const bool mapped = (int)blockIdx.x < nmap;
+  const int stride = mapped ? 0 : ((int)gridDim.x - nmap) * 4;
+  for (int r = mapped ? 0 : ((int)blockIdx.x - nmap) * 4 + wib;; r += stride) {
+    int2 e;
+    if (mapped) {
+      e = map[blockIdx.x];
+      e.y += wib;
+    } else {
+      if (r >= *redo_n) break;
+      e = redo_list[r];
+    }
+    copy_words(&sC[wib], cols + e.x, sizeof(Colony), wib * 32, 32);
+    copy_words(&sA[wib], ants + e.x, sizeof(Ants), wib * 32, 32);
+    __syncwarp();
+    ants_arr_body<KW, false>(sC[wib], sA[wib], e.y, smem + (size_t)wib * per_warp);
+    __syncwarp();
+    if (mapped) break;
+  }
 }
 
 }  // namespace
@@ -685,6 +762,80 @@ cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s) {
   else
     k_ants<32, false><<<grid, block, smem, s>>>(C, A);
   return cudaGetLastError();
+}
+
+cudaError_t launch_ants_blk_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int blocks,
+                                  int2* redo_list, int32_t* redo_n, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (kw == 16)
+    k_ants_blk_b<16><<<blocks, 32 * kAntWarps, smem, s>>>(cols, ants, map, redo_list, redo_n);
+  else
+    k_ants_blk_b<32><<<blocks, 32 * kAntWarps, smem, s>>>(cols, ants, map, redo_list, redo_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ants_arr_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int nmap,
+                                  int redo_blocks, const int2* redo_list, const int32_t* redo_n,
+                                  size_t per_warp, cudaStream_t s) {
+  const int blocks = nmap + redo_blocks;
+  if (blocks <= 0) return cudaSuccess;
+  const size_t smem = 4 * per_warp;
+  if (kw == 16)
+    k_ants_b<16><<<blocks, 128, smem, s>>>(cols, ants, map, nmap, redo_list, redo_n, per_warp);
+  else
+    k_ants_b<32><<<blocks, 128, smem, s>>>(cols, ants, map, nmap, redo_list, redo_n, per_warp);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory of the batch segment-table kernel that still lets
+// as many blocks reside per SM as its registers allow.
+size_t ants_blk_batch_smem(int kw) {
+  const void* f = kw == 16 ? reinterpret_cast<const void*>(k_ants_blk_b<16>)
+                           : reinterpret_cast<const void*>(k_ants_blk_b<32>);
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  const int threads = 32 * kAntWarps;
+  int blocks = regs_sm / (fa.numRegs > 0 ? fa.numRegs * threads : threads);
+  if (blocks < 1) blocks = 1;
+  for (; blocks >= 1; --blocks) {
+    long long S = (long long)smem_sm / blocks - reserved - (long long)fa.sharedSizeBytes;
+    S &= ~127LL;
+    for (int tries = 0; tries < 8 && S > 0; ++tries, S -= 256) {
+      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, (size_t)S) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (nb >= blocks) return (size_t)S;
+    }
+  }
+  return 0;
+}
+
+cudaError_t prepare_ants_batch(int kw, size_t smem_blk, size_t smem_arr) {
+  cudaError_t e;
+  if (kw == 16) {
+    e = cudaFuncSetAttribute(k_ants_blk_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ants_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+  } else {
+    e = cudaFuncSetAttribute(k_ants_blk_b<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ants_b<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+  }
+  return e;
 }
 
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr) {

@@ -10,6 +10,7 @@
 
 #include "faco.h"
 #include "launch.h"
+#include "multi.h"
 
 using namespace faco;
 
@@ -107,16 +108,9 @@ Colony colony_view(const faco_ctx* c) {
   C.grid = c->grid;
   C.cell_start = c->cell_start;
   C.cell_pts = c->cell_pts;
+  C.tmp_route = c->tmp_route;
+  C.tmp_pos = c->tmp_pos;
   return C;
-}
-
-int check_params(const faco_params& p) {
-  if (!(p.rho > 0.0f && p.rho < 1.0f)) return FACO_E_ARG;
-  if (!(p.p_best > 0.0 && p.p_best < 1.0)) return FACO_E_ARG;
-  if (!(p.p_source_gb >= 0.0 && p.p_source_gb <= 1.0)) return FACO_E_ARG;
-  if (p.min_new_edges < 1 || p.bl_size < 0 || p.bl_size > 128) return FACO_E_ARG;
-  if (p.seg_cap < -1 || (p.seg_cap > 0 && p.seg_cap < 8) || p.seg_cap > 4096) return FACO_E_ARG;
-  return FACO_OK;
 }
 
 void free_ants(faco_ctx* c) {
@@ -173,7 +167,7 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
   faco_params prm;
   faco_params_default(&prm);
   if (p) prm = *p;
-  int rc = check_params(prm);
+  int rc = check_faco_params(prm);
   if (rc != FACO_OK) return rc;
   if (!on_device) {
     for (int64_t i = 0; i < 2 * (int64_t)n; ++i)
@@ -394,7 +388,7 @@ int enqueue_iteration(faco_ctx* c, int parts) {
   if (parts & 1) CK(launch_ants(C, c->A, c->stream));
   if (parts & 2) {
     CK(launch_best(C, c->A, c->stream));
-    CK(launch_source(C, c->A, c->tmp_route, c->tmp_pos, c->stream));
+    CK(launch_source(C, c->A, c->stream));
     CK(launch_rows(C, 1, c->stream));
     CK(launch_scan_P(C, c->stream));
   }

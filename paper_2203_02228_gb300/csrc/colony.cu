@@ -15,8 +15,7 @@ namespace {
 //   tau' = max(tau_min, min(tau_max, fmaf(rho, tau, delta * [edge in source])))
 //   Wsrc[p][s] = tau' * eta,  Csrc[p][s] = source position of cand[u][s].
 // update = 0 only sets tau = tau_max (Alg 2 set-up).
-__global__ void k_rows(Colony C, int update) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
   const int n = C.n;
   if (p >= n) return;
   const int u = C.src_route[p];
@@ -50,7 +49,7 @@ __global__ void k_rows(Colony C, int update) {
 }
 
 // Exclusive prefix sums of the source edge lengths (one block).
-__global__ void __launch_bounds__(1024) k_scan_P(Colony C) {
+__device__ __forceinline__ void scan_P_body(const Colony& C) {
   __shared__ int64_t warp_tot[32];
   const int n = C.n, t = threadIdx.x, T = blockDim.x;
   const int chunk = (n + T - 1) / T;
@@ -94,7 +93,7 @@ __device__ __forceinline__ void set_limits(const Colony& C, DevState* st, int64_
 
 // Iteration best (shortest, lowest ant on ties), global best + limits,
 // source choice, deposit amount, history row (one block).
-__global__ void __launch_bounds__(1024) k_best(Colony C, Ants A) {
+__device__ __forceinline__ void best_body(const Colony& C, const Ants& A) {
   __shared__ int64_t sl[32];
   __shared__ int32_t sa[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -156,8 +155,9 @@ __global__ void __launch_bounds__(1024) k_best(Colony C, Ants A) {
 // segment table (source positions -> node ids of the current source), or
 // from the ant's arrays when it was built with them.  Skipped when neither
 // the global best nor the source will take it.
-__global__ void k_best_tour(Colony C, Ants A, int32_t* tmp_route, int32_t* tmp_pos) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void best_tour_body(const Colony& C, const Ants& A, int t) {
+  int32_t* tmp_route = C.tmp_route;
+  int32_t* tmp_pos = C.tmp_pos;
   const int n = C.n;
   const DevState* st = C.st;
   if (t >= n || (!st->gb_improved && st->use_gb)) return;
@@ -193,8 +193,9 @@ __global__ void k_best_tour(Colony C, Ants A, int32_t* tmp_route, int32_t* tmp_p
 
 // Global best <- iteration best when improved; source <- global best or
 // iteration best (routes and positions).
-__global__ void k_source(Colony C, const int32_t* tmp_route, const int32_t* tmp_pos) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void source_body(const Colony& C, int i) {
+  const int32_t* tmp_route = C.tmp_route;
+  const int32_t* tmp_pos = C.tmp_pos;
   const int n = C.n;
   if (i >= n) return;
   const DevState* st = C.st;
@@ -211,8 +212,7 @@ __global__ void k_source(Colony C, const int32_t* tmp_route, const int32_t* tmp_
   }
 }
 
-__global__ void k_state_init(Colony C, const int64_t* len) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void state_init_body(const Colony& C, const int64_t* len) {
   DevState* st = C.st;
   const int64_t L = *len;
   st->iter = 0;
@@ -226,6 +226,116 @@ __global__ void k_state_init(Colony C, const int64_t* len) {
   st->error = 0;
   set_limits(C, st, L);
   st->delta = __double2float_rn(1.0 / (double)L);
+}
+
+// ---------------------------------------------------------------------
+// Kernels of one colony (descriptor by value) and of a batch (each block
+// reads its colony, and its block within the colony, from a block map).
+// ---------------------------------------------------------------------
+__global__ void k_rows(Colony C, int update) { rows_body(C, blockIdx.x * blockDim.x + threadIdx.x, update); }
+
+__global__ void __launch_bounds__(1024) k_scan_P(Colony C) { scan_P_body(C); }
+
+__global__ void __launch_bounds__(1024) k_best(Colony C, Ants A) { best_body(C, A); }
+
+__global__ void k_best_tour(Colony C, Ants A) { best_tour_body(C, A, blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_source(Colony C) { source_body(C, blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_state_init(Colony C, const int64_t* len) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) state_init_body(C, len);
+}
+
+__global__ void k_rows_b(const Colony* cols, const int2* map, int update) {
+  const int2 e = map[blockIdx.x];
+  const Colony C = cols[e.x];
+  rows_body(C, e.y * blockDim.x + threadIdx.x, update);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_P_b(const Colony* cols) {
+  const Colony C = cols[blockIdx.x];
+  scan_P_body(C);
+}
+
+// Also empties the redo list of the batch's per-ant kernels (they have all
+// finished when this kernel runs).
+__global__ void __launch_bounds__(1024) k_best_b(const Colony* cols, const Ants* ants, int32_t* redo_n) {
+  const Colony C = cols[blockIdx.x];
+  const Ants A = ants[blockIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && redo_n) *redo_n = 0;
+  best_body(C, A);
+}
+
+__global__ void k_best_tour_b(const Colony* cols, const Ants* ants, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const Colony C = cols[e.x];
+  const Ants A = ants[e.x];
+  best_tour_body(C, A, e.y * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_source_b(const Colony* cols, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const Colony C = cols[e.x];
+  source_body(C, e.y * blockDim.x + threadIdx.x);
+}
+
+// Batch set-up: positions of the initial tour (into src_pos, the local
+// search's position array), its length, the colony state, and source and
+// global best <- initial tour.
+__global__ void k_init_pos_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  if (i < C.n) C.src_pos[sets[e.x].init_route[i]] = i;
+}
+
+__global__ void k_init_len_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  const int32_t* route = sets[e.x].init_route;
+  int64_t d = 0;
+  if (i < C.n) d = euc2d(C.xy[route[i]], C.xy[route[i + 1 == C.n ? 0 : i + 1]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += shfl64_xor(d, o);
+  if ((threadIdx.x & 31) == 0 && d)
+    atomicAdd(reinterpret_cast<unsigned long long*>(sets[e.x].len), (unsigned long long)d);
+}
+
+__global__ void k_state_init_b(const Colony* cols, const ColonySetup* sets, int count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const Colony C = cols[c];
+  state_init_body(C, sets[c].len);
+}
+
+__global__ void k_init_routes_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  if (i >= C.n) return;
+  const int v = sets[e.x].init_route[i];
+  C.src_route[i] = v;
+  C.gb_route[i] = v;
+  C.src_pos[v] = i;
+  C.gb_pos[v] = i;
+}
+
+// Batch results: every colony's global-best tour packed at node_off[c];
+// lengths and the union of the device error flags.
+__global__ void k_pack_tours_b(const Colony* cols, const int2* map, const int64_t* node_off, int32_t* out) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  if (i < C.n) out[node_off[e.x] + i] = C.gb_route[i];
+}
+
+__global__ void k_pack_state_b(const Colony* cols, int count, int64_t* lens, int32_t* err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const DevState* st = cols[c].st;
+  lens[c] = st->gb_len;
+  if (st->error) atomicOr(err, st->error);
 }
 
 __global__ void k_positions(const int32_t* route, int32_t* pos, int n) {
@@ -259,10 +369,43 @@ cudaError_t launch_best(const Colony& C, const Ants& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_source(const Colony& C, const Ants& A, int32_t* tmp_route, int32_t* tmp_pos,
-                          cudaStream_t s) {
-  k_best_tour<<<(C.n + 255) / 256, 256, 0, s>>>(C, A, tmp_route, tmp_pos);
-  k_source<<<(C.n + 255) / 256, 256, 0, s>>>(C, tmp_route, tmp_pos);
+cudaError_t launch_source(const Colony& C, const Ants& A, cudaStream_t s) {
+  k_best_tour<<<(C.n + 255) / 256, 256, 0, s>>>(C, A);
+  k_source<<<(C.n + 255) / 256, 256, 0, s>>>(C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colony_update_batch(const Colony* cols, const Ants* ants, int count, const int2* map256,
+                                       int nmap256, int32_t* redo_n, cudaStream_t s) {
+  k_best_b<<<count, 256, 0, s>>>(cols, ants, redo_n);
+  k_best_tour_b<<<nmap256, 256, 0, s>>>(cols, ants, map256);
+  k_source_b<<<nmap256, 256, 0, s>>>(cols, map256);
+  k_rows_b<<<nmap256, 256, 0, s>>>(cols, map256, 1);
+  k_scan_P_b<<<count, 256, 0, s>>>(cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batch(const Colony* cols, int count, const int2* map256, int nmap256,
+                              const int64_t* node_off, int32_t* tours, int64_t* lens, int32_t* err,
+                              cudaStream_t s) {
+  if (tours) k_pack_tours_b<<<nmap256, 256, 0, s>>>(cols, map256, node_off, tours);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  k_pack_state_b<<<(count + 127) / 128, 128, 0, s>>>(cols, count, lens, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colony_init_batch(const Colony* cols, const ColonySetup* sets, int count, const int2* map256,
+                                     int nmap256, int stage, cudaStream_t s) {
+  if (stage == 0) {  // positions of the initial tour, before its local search
+    k_init_pos_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+  } else {  // after it: length, state, source and global best, rows, prefix sums
+    k_init_len_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+    k_state_init_b<<<(count + 127) / 128, 128, 0, s>>>(cols, sets, count);
+    k_init_routes_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+    k_rows_b<<<nmap256, 256, 0, s>>>(cols, map256, 0);
+    k_scan_P_b<<<count, 256, 0, s>>>(cols);
+  }
   return cudaGetLastError();
 }
 

@@ -87,6 +87,25 @@ struct Colony {
   Grid grid;             // point grid of the candidate-list build
   const int32_t* cell_start;  // [cells+1]
   const int32_t* cell_pts;    // [n] node ids by cell
+  int32_t* tmp_route;    // [n] iteration-best tour, materialised
+  int32_t* tmp_pos;      // [n]
+};
+
+// Set-up buffers of one colony of a batch: the candidate lists and the
+// initial tour of every colony are built by the same launches.
+struct ColonySetup {
+  int32_t* cell_cnt;     // [cells] counts, then the fill cursor
+  int32_t* cell_start;   // [cells+1]
+  int32_t* cell_pts;     // [n]
+  int32_t* cand;         // [n][k]
+  int32_t* backup;       // [n][bl]
+  float* eta;            // [n][k]
+  int32_t* init_route;   // [n] nearest-neighbour tour, then locally optimal
+  int32_t* queue;        // [n] local search of the initial tour
+  uint8_t* flags;        // [n]
+  int32_t* logb;         // [n]
+  int64_t* len;          // length of the initial tour
+  int32_t* bb;           // [5] min x, min y, max x, max y, out-of-range flag
 };
 
 // Per-ant buffers of one ant count.

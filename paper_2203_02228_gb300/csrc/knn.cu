@@ -16,13 +16,13 @@ namespace faco {
 
 namespace {
 
-__global__ void k_bbox_check(const int2* xy, int n, int32_t* out5) {
-  int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, bad = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int2 p = xy[i];
-    mnx = min(mnx, p.x); mny = min(mny, p.y); mxx = max(mxx, p.x); mxy = max(mxy, p.y);
-    bad |= (p.x < 0 || p.y < 0 || p.x >= (1 << 24) || p.y >= (1 << 24));
-  }
+__device__ __forceinline__ void bbox_add(int2 p, int& mnx, int& mny, int& mxx, int& mxy, int& bad) {
+  mnx = min(mnx, p.x); mny = min(mny, p.y); mxx = max(mxx, p.x); mxy = max(mxy, p.y);
+  bad |= (p.x < 0 || p.y < 0 || p.x >= (1 << 24) || p.y >= (1 << 24));
+}
+
+// Warp reduction of a partial bounding box into out5 (atomics).
+__device__ __forceinline__ void bbox_flush(int mnx, int mny, int mxx, int mxy, int bad, int32_t* out5) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mnx = min(mnx, __shfl_xor_sync(kFull, mnx, o));
@@ -40,6 +40,13 @@ __global__ void k_bbox_check(const int2* xy, int n, int32_t* out5) {
   }
 }
 
+__global__ void k_bbox_check(const int2* xy, int n, int32_t* out5) {
+  int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    bbox_add(xy[i], mnx, mny, mxx, mxy, bad);
+  bbox_flush(mnx, mny, mxx, mxy, bad, out5);
+}
+
 __device__ __forceinline__ int cell_of(const Grid& g, int2 p) {
   return ((p.y - g.miny) / g.cs) * g.gx + (p.x - g.minx) / g.cs;
 }
@@ -49,8 +56,9 @@ __global__ void k_cell_count(const int2* xy, int n, Grid g, int32_t* count) {
   if (i < n) atomicAdd(&count[cell_of(g, xy[i])], 1);
 }
 
-// Exclusive scan of `count` into `start` (start[len] = total), one block.
-__global__ void __launch_bounds__(1024) k_scan_i32(const int32_t* count, int32_t* start, int len) {
+// Exclusive scan of `count` into `start` (start[len] = total), one block;
+// also into `cursor` when given (which may be `count` itself).
+__device__ __forceinline__ void scan_i32_body(int32_t* count, int32_t* start, int len, int32_t* cursor) {
   __shared__ int32_t warp_tot[32];
   const int t = threadIdx.x, T = blockDim.x;
   const int chunk = (len + T - 1) / T;
@@ -78,10 +86,16 @@ __global__ void __launch_bounds__(1024) k_scan_i32(const int32_t* count, int32_t
   __syncthreads();
   int32_t run = (incl - s) + (w > 0 ? warp_tot[w - 1] : 0);
   for (int i = lo; i < hi; ++i) {
+    const int32_t ci = count[i];
     start[i] = run;
-    run += count[i];
+    if (cursor) cursor[i] = run;
+    run += ci;
   }
   if (t == T - 1) start[len] = warp_tot[(T >> 5) - 1];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_i32(int32_t* count, int32_t* start, int len) {
+  scan_i32_body(count, start, len, nullptr);
 }
 
 __global__ void k_cell_fill(const int2* xy, int n, Grid g, int32_t* cursor, int32_t* pts) {
@@ -89,10 +103,9 @@ __global__ void k_cell_fill(const int2* xy, int n, Grid g, int32_t* cursor, int3
   if (i < n) pts[atomicAdd(&cursor[cell_of(g, xy[i])], 1)] = i;
 }
 
-__global__ void __launch_bounds__(128) k_knn(const int2* xy, int n, Grid g, const int32_t* start,
-                                             const int32_t* pts, int k, int bl, int32_t* cand,
-                                             int32_t* backup, float* eta) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void knn_body(const int2* xy, int n, const Grid& g, const int32_t* start,
+                                         const int32_t* pts, int k, int bl, int32_t* cand, int32_t* backup,
+                                         float* eta, int u) {
   if (u >= n) return;
   const int K = k + bl;
   uint64_t bm[kMaxKnn];
@@ -151,7 +164,100 @@ __global__ void __launch_bounds__(128) k_knn(const int2* xy, int n, Grid g, cons
   for (int j = 0; j < bl; ++j) backup[(size_t)u * bl + j] = bi[k + j];
 }
 
+__global__ void __launch_bounds__(128) k_knn(const int2* xy, int n, Grid g, const int32_t* start,
+                                             const int32_t* pts, int k, int bl, int32_t* cand,
+                                             int32_t* backup, float* eta) {
+  knn_body(xy, n, g, start, pts, k, bl, cand, backup, eta, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------
+// Batch: the same steps for every colony of a batch; each block reads its
+// colony and its block within the colony from a block map.
+// ---------------------------------------------------------------------
+__global__ void k_bbox_init_b(const ColonySetup* sets, int count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  int32_t* b = sets[c].bb;
+  b[0] = INT_MAX; b[1] = INT_MAX; b[2] = INT_MIN; b[3] = INT_MIN; b[4] = 0;
+}
+
+__global__ void k_bbox_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const int n = cols[e.x].n;
+  int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, bad = 0;
+  if (i < n) bbox_add(cols[e.x].xy[i], mnx, mny, mxx, mxy, bad);
+  bbox_flush(mnx, mny, mxx, mxy, bad, sets[e.x].bb);
+}
+
+// Grid of each colony from its bounding box, by the rule of the one-colony
+// set-up: G = ceil(sqrt(n / 2)) cells per side of the square of the larger
+// extent, so gx, gy <= G.
+__global__ void k_grid_b(Colony* cols, const ColonySetup* sets, int count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const int32_t* b = sets[c].bb;
+  const int n = cols[c].n;
+  const int64_t ext = (int64_t)max(b[2] - b[0], b[3] - b[1]) + 1;
+  int64_t G = (int64_t)ceil(sqrt((double)n / 2.0));
+  if (G < 1) G = 1;
+  Grid g;
+  g.minx = b[0];
+  g.miny = b[1];
+  g.cs = (int32_t)((ext + G - 1) / G);
+  if (g.cs < 1) g.cs = 1;
+  g.gx = (b[2] - b[0]) / g.cs + 1;
+  g.gy = (b[3] - b[1]) / g.cs + 1;
+  cols[c].grid = g;
+}
+
+__global__ void k_cell_count_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  if (i < C.n) atomicAdd(&sets[e.x].cell_cnt[cell_of(C.grid, C.xy[i])], 1);
+}
+
+__global__ void __launch_bounds__(1024) k_cell_scan_b(const Colony* cols, const ColonySetup* sets) {
+  const ColonySetup S = sets[blockIdx.x];
+  const Grid g = cols[blockIdx.x].grid;
+  scan_i32_body(S.cell_cnt, S.cell_start, g.gx * g.gy, S.cell_cnt);
+}
+
+__global__ void k_cell_fill_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const int i = e.y * blockDim.x + threadIdx.x;
+  const Colony C = cols[e.x];
+  if (i < C.n) sets[e.x].cell_pts[atomicAdd(&sets[e.x].cell_cnt[cell_of(C.grid, C.xy[i])], 1)] = i;
+}
+
+__global__ void __launch_bounds__(128) k_knn_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
+  const int2 e = map[blockIdx.x];
+  const Colony C = cols[e.x];
+  const ColonySetup S = sets[e.x];
+  knn_body(C.xy, C.n, C.grid, S.cell_start, S.cell_pts, C.k, C.bl, S.cand, S.backup, S.eta,
+           e.y * blockDim.x + threadIdx.x);
+}
+
 }  // namespace
+
+cudaError_t launch_grid_batch(Colony* cols, const ColonySetup* sets, int count, const int2* map256, int nmap256,
+                              cudaStream_t s) {
+  k_bbox_init_b<<<(count + 127) / 128, 128, 0, s>>>(sets, count);
+  k_bbox_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+  k_grid_b<<<(count + 127) / 128, 128, 0, s>>>(cols, sets, count);
+  return cudaGetLastError();
+}
+
+// The cell counts must be zero on entry.
+cudaError_t build_lists_batch(const Colony* cols, const ColonySetup* sets, int count, const int2* map256,
+                              int nmap256, const int2* map128, int nmap128, cudaStream_t s) {
+  k_cell_count_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+  k_cell_scan_b<<<count, 256, 0, s>>>(cols, sets);
+  k_cell_fill_b<<<nmap256, 256, 0, s>>>(cols, sets, map256);
+  k_knn_b<<<nmap128, 128, 0, s>>>(cols, sets, map128);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bbox_check(const int2* xy, int n, int32_t* out5, cudaStream_t s) {
   const int32_t init[5] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN, 0};

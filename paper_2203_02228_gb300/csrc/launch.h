@@ -12,15 +12,28 @@ namespace faco {
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s);
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr);
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs);
+cudaError_t launch_ants_blk_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int blocks,
+                                  int2* redo_list, int32_t* redo_n, size_t smem, cudaStream_t s);
+cudaError_t launch_ants_arr_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int nmap,
+                                  int redo_blocks, const int2* redo_list, const int32_t* redo_n,
+                                  size_t per_warp, cudaStream_t s);
+cudaError_t prepare_ants_batch(int kw, size_t smem_blk, size_t smem_arr);
+size_t ants_blk_batch_smem(int kw);
 
 // colony.cu
 cudaError_t launch_rows(const Colony& C, int update, cudaStream_t s);
 cudaError_t launch_scan_P(const Colony& C, cudaStream_t s);
 cudaError_t launch_best(const Colony& C, const Ants& A, cudaStream_t s);
-cudaError_t launch_source(const Colony& C, const Ants& A, int32_t* tmp_route, int32_t* tmp_pos,
-                          cudaStream_t s);
+cudaError_t launch_source(const Colony& C, const Ants& A, cudaStream_t s);
 cudaError_t launch_state_init(const Colony& C, const int64_t* len, cudaStream_t s);
 cudaError_t launch_positions(const int32_t* route, int32_t* pos, int n, cudaStream_t s);
+cudaError_t launch_colony_update_batch(const Colony* cols, const Ants* ants, int count, const int2* map256,
+                                       int nmap256, int32_t* redo_n, cudaStream_t s);
+cudaError_t launch_colony_init_batch(const Colony* cols, const ColonySetup* sets, int count, const int2* map256,
+                                     int nmap256, int stage, cudaStream_t s);
+cudaError_t launch_pack_batch(const Colony* cols, int count, const int2* map256, int nmap256,
+                              const int64_t* node_off, int32_t* tours, int64_t* lens, int32_t* err,
+                              cudaStream_t s);
 cudaError_t launch_tour_length(const int2* xy, const int32_t* route, int n, int64_t* out,
                                cudaStream_t s);
 
@@ -30,6 +43,11 @@ cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int
                         int32_t* cell_start, int32_t* cell_pts, int32_t* cand, int32_t* backup,
                         float* eta, cudaStream_t s);
 
+cudaError_t launch_grid_batch(Colony* cols, const ColonySetup* sets, int count, const int2* map256, int nmap256,
+                              cudaStream_t s);
+cudaError_t build_lists_batch(const Colony* cols, const ColonySetup* sets, int count, const int2* map256,
+                              int nmap256, const int2* map128, int nmap128, cudaStream_t s);
+
 // tour.cu
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
                            int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
@@ -37,6 +55,8 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, int k, int oropt, int verify,
                            int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s);
+cudaError_t launch_init_tour_batch(const Colony* cols, const ColonySetup* sets, int count, int max_n, int stage,
+                                   cudaStream_t s);
 cudaError_t launch_test_kernels(int what, const void* in, void* out, int count, int width,
                                 uint64_t seed, cudaStream_t s);
 

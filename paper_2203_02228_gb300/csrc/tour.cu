@@ -17,12 +17,9 @@ namespace faco {
 
 namespace {
 
-__global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int32_t* cand, int k,
-                                                const int32_t* backup, int bl, int32_t* route,
-                                                uint32_t* vis_g, Grid g, const int32_t* cstart,
-                                                const int32_t* cpts) {
-  extern __shared__ uint32_t sv[];
-  uint32_t* vis = vis_g ? vis_g : sv;
+__device__ __forceinline__ void nn_tour_body(const int2* xy, int n, const int32_t* cand, int k,
+                                             const int32_t* backup, int bl, int32_t* route, uint32_t* vis,
+                                             const Grid& g, const int32_t* cstart, const int32_t* cpts) {
   const int lane = lane_id();
   const int words = (n + 31) >> 5;
   for (int i = lane; i < words; i += 32) vis[i] = 0;
@@ -84,6 +81,22 @@ __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int
   }
 }
 
+__global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int32_t* cand, int k,
+                                                const int32_t* backup, int bl, int32_t* route,
+                                                uint32_t* vis_g, Grid g, const int32_t* cstart,
+                                                const int32_t* cpts) {
+  extern __shared__ uint32_t sv[];
+  nn_tour_body(xy, n, cand, k, backup, bl, route, vis_g ? vis_g : sv, g, cstart, cpts);
+}
+
+// Batch: one warp per colony, visited bits in shared memory.
+__global__ void __launch_bounds__(32) k_nn_tour_b(const Colony* cols, const ColonySetup* sets) {
+  extern __shared__ uint32_t sv[];
+  const Colony C = cols[blockIdx.x];
+  const ColonySetup S = sets[blockIdx.x];
+  nn_tour_body(C.xy, C.n, S.cand, C.k, S.backup, C.bl, S.init_route, sv, C.grid, S.cell_start, S.cell_pts);
+}
+
 // Reverse the forward span x..y (or its complement) with the whole block.
 __device__ void cta_flip(ArrTour& T, int x, int y) {
   const int n = T.n;
@@ -129,9 +142,9 @@ __device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4) {
 // queue order up to and including the first one that found a move, which
 // is applied.  Nothing changes the tour between the confirmed evaluations,
 // so the result is exactly that of popping one node at a time.
-__global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand, int k,
-                                                  int oropt, int verify, int32_t* route, int32_t* pos,
-                                                  int32_t* queue, uint8_t* flags, int32_t* logb) {
+__device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_t* cand, int k, int oropt,
+                                             int verify, int32_t* route, int32_t* pos, int32_t* queue,
+                                             uint8_t* flags, int32_t* logb) {
   __shared__ int64_t s_gain[32];
   __shared__ int s_mv[32][8];
   __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win;
@@ -244,6 +257,19 @@ __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const i
   for (int i = tid; i < nl; i += blockDim.x) flags[logb[i]] = 0;
 }
 
+__global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand, int k,
+                                                  int oropt, int verify, int32_t* route, int32_t* pos,
+                                                  int32_t* queue, uint8_t* flags, int32_t* logb) {
+  init_ls_body(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
+}
+
+// Batch: one block per colony; positions of the initial tour in src_pos.
+__global__ void __launch_bounds__(1024) k_init_ls_b(const Colony* cols, const ColonySetup* sets) {
+  const Colony C = cols[blockIdx.x];
+  const ColonySetup S = sets[blockIdx.x];
+  init_ls_body(C.xy, C.n, S.cand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags, S.logb);
+}
+
 // what = 0: Philox draws   in: uint32 [count][4] = (idx, ant, iter, tag) -> out uint32
 // what = 1: EUC_2D         in: int32 [count][4] = (x1, y1, x2, y2)       -> out int32
 // what = 2: roulette       in: float [count][width + 1] (weights, u)     -> out int32
@@ -290,6 +316,21 @@ cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, int k, in
                            int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s) {
   k_init_ls<<<1, 1024, 0, s>>>(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_tour_batch(const Colony* cols, const ColonySetup* sets, int count, int max_n, int stage,
+                                   cudaStream_t s) {
+  if (stage == 0) {
+    const size_t smem = (size_t)((max_n + 31) >> 5) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_nn_tour_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_nn_tour_b<<<count, 32, smem, s>>>(cols, sets);
+  } else {
+    k_init_ls_b<<<count, 1024, 0, s>>>(cols, sets);
+  }
   return cudaGetLastError();
 }
 

@@ -112,6 +112,14 @@ def batch_sizes(count: int, seed: int = 4000, lo: int = 200, hi: int = 20_000) -
     return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), count))).astype(np.int32)
 
 
+def batch_instances(count: int, seed: int = 4000, lo: int = 200, hi: int = 20_000,
+                    side: int = 1_000_000) -> list:
+    """`count` independent uniform instances with log-uniform sizes in [lo, hi];
+    instance i is uniform(n_i, seed * 1000 + i + 1, side)."""
+    sizes = batch_sizes(count, seed, lo, hi)
+    return [uniform(int(n), seed=seed * 1000 + i + 1, side=side) for i, n in enumerate(sizes)]
+
+
 def lattice(rows: int, cols: int, step: int = 10) -> np.ndarray:
     """Regular grid: maximal distance ties (edge case for neighbour order)."""
     y, x = np.divmod(np.arange(rows * cols), cols)
@@ -126,6 +134,21 @@ WORKLOADS = {
     "stippled200k": dict(kind="stippled", n=200_000, seed=3003, blobs=256, ridges=16,
                          side=100_000, ants=2048, iters=50),
 }
+
+
+# The batched workload: independent uniform instances run together; colony i
+# uses Philox seed seed0 + i.
+BATCH_WORKLOADS = {
+    "batch512": dict(count=512, seed=4000, lo=200, hi=20_000, side=1_000_000, k=16, ants=64, iters=100,
+                     seed0=1),
+}
+
+
+def batch_workload(name: str):
+    """(instances, seeds) of a batched workload."""
+    w = BATCH_WORKLOADS[name]
+    xs = batch_instances(w["count"], w["seed"], w["lo"], w["hi"], w["side"])
+    return xs, np.arange(w["seed0"], w["seed0"] + w["count"], dtype=np.uint64)
 
 
 def workload_points(name: str) -> np.ndarray:

@@ -15,9 +15,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "faco.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(faco_\w+)\s*\(", src, flags=re.M)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(faco_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -29,6 +34,7 @@ def lib():
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert "faco_create" in names and "faco_iterate" in names and "faco_best" in names
+    assert "faco_batch_create" in names and "faco_batch_iterate" in names and "faco_batch_best" in names
     for name in names:
         assert hasattr(lib, name), name
 
@@ -72,4 +78,55 @@ def test_no_cpu_fallback_without_gpu(lib):
     xy = np.stack([np.arange(50), np.arange(50) * 3 % 17], 1).astype(np.int32)
     h = ctypes.c_void_p()
     rc = lib.faco_create(xy.ctypes.data_as(ctypes.c_void_p), 50, 16, ctypes.byref(h))
+    assert rc == _lib.FACO_E_CUDA
+
+
+def _batch_args(arrays):
+    ptrs = (ctypes.c_void_p * len(arrays))(*[a.ctypes.data for a in arrays])
+    ns = np.array([a.shape[0] for a in arrays], np.int32)
+    return ctypes.cast(ptrs, ctypes.c_void_p), ns
+
+
+def test_batch_invalid_arguments_are_rejected(lib):
+    a = np.stack([np.arange(20), np.arange(20) * 7 % 13], 1).astype(np.int32)
+    b = np.stack([np.arange(30), np.arange(30) * 5 % 11], 1).astype(np.int32)
+    h = ctypes.c_void_p()
+    P = lambda x: x.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    ptrs, ns = _batch_args([a, b])
+    assert lib.faco_batch_create(None, P(ns), 2, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_create(ptrs, None, 2, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_create(ptrs, P(ns), 0, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_create(ptrs, P(ns), 2, 1, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_create(ptrs, P(ns), 2, 33, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    small = ns.copy()
+    small[1] = 2
+    assert lib.faco_batch_create(ptrs, P(small), 2, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    big = ns.copy()
+    big[0] = 262145
+    assert lib.faco_batch_create(ptrs, P(big), 2, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_SIZE
+    # k > 16 with an instance whose list is clamped to 16 or fewer: two roulette widths
+    tiny = np.stack([np.arange(12), np.arange(12)], 1).astype(np.int32)
+    ptrs2, ns2 = _batch_args([a, tiny])
+    assert lib.faco_batch_create(ptrs2, P(ns2), 2, 24, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    bad = b.copy()
+    bad[4, 0] = 1 << 24
+    ptrs3, ns3 = _batch_args([a, bad])
+    assert lib.faco_batch_create(ptrs3, P(ns3), 2, 16, None, None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    for field, val in (("keep_ant_tours", 1), ("keep_pre_ls", 1), ("seg_cap", 64), ("rho", 1.0)):
+        p = params_default(**{field: val})
+        assert lib.faco_batch_create(ptrs, P(ns), 2, 16, ctypes.byref(p), None, ctypes.byref(h)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_iterate(None, 4, 1) == _lib.FACO_E_ARG
+    assert lib.faco_batch_best(None, 0, None, 0, None) == _lib.FACO_E_ARG
+    assert lib.faco_batch_set_plan(None, 0) == _lib.FACO_E_ARG
+
+
+def test_batch_no_cpu_fallback_without_gpu(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    a = np.stack([np.arange(40), np.arange(40) * 7 % 13], 1).astype(np.int32)
+    ptrs, ns = _batch_args([a, a])
+    h = ctypes.c_void_p()
+    rc = lib.faco_batch_create(ptrs, ns.ctypes.data_as(ctypes.c_void_p), 2, 16, None, None, ctypes.byref(h))
     assert rc == _lib.FACO_E_CUDA
