@@ -189,6 +189,82 @@ def run_reference(args, W):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(args, stream, flush, barrier):
+    """The 512-instance batch (one Batch: set-up of every instance, 64 ants x
+    100 iterations in one graph launch, every tour back to the host) against
+    the plain one-instance-at-a-time loop (Colony per instance through the
+    same host API) on a stratified sample of the same instances."""
+    import torch
+
+    from paper_2203_02228_gb300 import Batch, Colony, inputs
+
+    w = inputs.BATCH_WORKLOADS["batch512"]
+    xs, seeds = inputs.batch_workload("batch512")
+    ants, iters, k = w["ants"], w["iters"], w["k"]
+    ns = np.array([x.shape[0] for x in xs])
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def run_batch():
+        b = Batch(xs, k, seeds=seeds, stream=stream)
+        b.iterate(ants, iters)
+        tours, lens = b.tours()
+        return b, tours, lens
+
+    for _ in range(2):  # the first also runs the kernel tuner (cached per process)
+        b, _, _ = run_batch()
+        b.close()
+    times, wall = [], []
+    for _ in range(max(1, args.batch_steps)):
+        flush.zero_()
+        barrier()
+        e0, e1 = ev(), ev()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        b, tours, lens = run_batch()
+        e1.record(stream)
+        e1.synchronize()
+        wall.append(time.perf_counter() - t0)
+        times.append(e0.elapsed_time(e1) / 1e3)
+        plan = b.plan()
+        launches = b.stats(0).kernel_launches
+        b.close()
+    t_batch = statistics.mean(wall)
+
+    # plain loop on every 8th instance by size: the sample spans the size range
+    order = np.argsort(ns, kind="stable")
+    sample = order[4::8]
+    Colony(xs[int(sample[0])], k, seed=int(seeds[sample[0]])).close()  # warm
+    flush.zero_()
+    barrier()
+    t0 = time.perf_counter()
+    plain = {}
+    for i in sample:
+        c = Colony(xs[int(i)], k, seed=int(seeds[i]), stream=stream)
+        c.iterate(ants, iters)
+        plain[int(i)] = c.best()
+        c.close()
+    t_plain = time.perf_counter() - t0
+    same = all(np.array_equal(plain[i][0], tours[i]) and plain[i][1] == lens[i] for i in plain)
+    inst_batch = len(xs) / t_batch
+    inst_plain = len(sample) / t_plain
+    return {
+        "workload": "batch512", "instances": len(xs), "n_range": [int(ns.min()), int(ns.max())],
+        "n_mean": float(ns.mean()), "ants": ants, "iterations": iters, "k": k,
+        "metric": "instances/sec (set-up + budget + tours to host)", "unit": "instances/s",
+        "value": inst_batch, "ms_per_batch": t_batch * 1e3, "device_ms_per_batch": statistics.mean(times) * 1e3,
+        "ant_solutions_per_s": len(xs) * ants * iters / t_batch,
+        "plain_loop": {"value": inst_plain, "unit": "instances/s", "sample": "%d of %d instances (every 8th by "
+                       "size), one Colony each through the same host API" % (len(sample), len(xs)),
+                       "seconds": t_plain},
+        "speedup_vs_plain": inst_batch / inst_plain,
+        "equal_results_on_sample": bool(same),
+        "mean_best_length": float(np.mean(lens)),
+        "plan": {"segment_table_colonies": int((plan == 0).sum()), "array_colonies": int((plan == 1).sum())},
+        "gpu_launches_per_batch": int(launches), "graph_launches_per_batch": 1,
+        "h2d_bytes_per_batch": int(8 * ns.sum()), "d2h_bytes_per_batch": int(4 * ns.sum() + 8 * len(xs)),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,7 +276,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-ants", type=int, default=32)
     ap.add_argument("--iters", type=int, default=0, help="override the iteration budget (testing only)")
+    ap.add_argument("--sections", default="main,batch", help="comma list of: main, batch")
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
+    sections = set(args.sections.split(","))
 
     from paper_2203_02228_gb300 import inputs
 
@@ -247,6 +326,14 @@ def main():
         prof = col.profile_read() if profile else (0.0, 0)
         col.close()
         return st, prof
+
+    if "main" not in sections:
+        out = {}
+        if "batch" in sections:
+            out["batched"] = bench_batched(args, stream, flush, barrier)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
 
     for _ in range(args.warmup):
         solve()
@@ -328,6 +415,10 @@ def main():
                "sample": "oracle set-up of the full instance (%.1f s) + 1 iteration of 32 ants (%.1f ms per "
                          "ant-solution), extrapolated to %d ants x %d iterations" % (tc, ti * 1e3, ants, iters)}
 
+    batched = None
+    if "batch" in sections and world == 1:
+        batched = bench_batched(args, stream, flush, barrier)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -337,7 +428,7 @@ def main():
                        "seed": 1, "l2": "flushed before every step (512 MB write)",
                        "parallelism": "independent colonies per rank" if world > 1 else "single colony"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clk,
+            "clocks": clk, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

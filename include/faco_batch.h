@@ -15,10 +15,11 @@
  *   faco_create_ex(coords_xy[i], ns[i], k, p_i, ...) followed by the same
  *   faco_iterate(ants, budget) calls,
  * where p_i is *p with seed = seeds[i] (or p->seed when seeds is NULL).
- * The kernel choice per colony (a block of four warps on a segment table
- * in shared memory, or one warp on explicit arrays; chosen per size class
- * by a timing autotuner or fixed with faco_batch_set_plan) changes only
- * the speed, never a result.
+ * The kernel choice per colony (a block of four warps per ant on a segment
+ * table in shared memory, or one warp per ant on explicit arrays compiled
+ * for 2, 4 or 8 resident blocks of four ants per SM; chosen per size class
+ * by a timing autotuner or fixed with faco_batch_set_plan) changes only the
+ * speed, never a result.
  *
  * Conventions are those of faco.h: int status returns, int32 (x, y)
  * coordinates in [0, 2^24), int64 lengths, work enqueued on p->stream (NULL
@@ -85,13 +86,16 @@ int faco_batch_stats(faco_batch* b, int32_t i, faco_stats* s);
 /* Pheromone of colony i, [n][k'] in candidate-list order. */
 int faco_batch_tau(faco_batch* b, int32_t i, float* tau);
 
-/* Kernel plan: mode -1 = autotune per size class (default), 0 = segment-
- * table blocks for every colony whose table fits, 1 = one warp per ant on
- * explicit arrays for every colony.  Takes effect at the next
- * faco_batch_iterate (re-planned and re-captured).  Errors: FACO_E_ARG. */
+/* Kernel plan: mode -1 = autotune per size class (default); 0 = segment-
+ * table blocks for every colony whose table fits (the others: mode 1);
+ * 1, 2, 3 = one warp per ant on explicit arrays, the kernel compiled for
+ * 2, 4, 8 resident blocks of four ants per SM (fewer registers per thread
+ * as the residency grows).  Takes effect at the next faco_batch_iterate
+ * (re-planned and re-captured; the ant counters restart from zero).
+ * Errors: FACO_E_ARG. */
 int faco_batch_set_plan(faco_batch* b, int32_t mode);
 
-/* The plan in use: `count` entries, 0 = segment-table block, 1 = arrays;
+/* The plan in use: `count` entries with the codes of faco_batch_set_plan;
  * -1 before the first faco_batch_iterate. */
 int faco_batch_get_plan(faco_batch* b, int32_t* variants);
 

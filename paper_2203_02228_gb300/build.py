@@ -35,17 +35,44 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _compile(args):
+    cmd, verbose = args
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles every translation unit in parallel, then links libfaco.so."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + NVCC_FLAGS + ["-shared", "-I", INCLUDE, "-o", tmp] + sources()
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    tag = "%d" % os.getpid()
+    objs, jobs = [], []
+    for src in sources():
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".%s.o" % tag)
+        objs.append(obj)
+        jobs.append(([nvcc] + NVCC_FLAGS + ["-I", INCLUDE, "-c", src, "-o", obj], verbose))
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(_compile, jobs))
+    failed = [r for r in results if r.returncode != 0]
+    try:
+        if failed:
+            sys.stderr.write(failed[0].stdout + failed[0].stderr)
+            raise subprocess.CalledProcessError(failed[0].returncode, failed[0].args)
+        tmp = LIB + ".tmp" + tag
+        link = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
+        if verbose:
+            print(" ".join(link), file=sys.stderr)
+        subprocess.run(link, check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

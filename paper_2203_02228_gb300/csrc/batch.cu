@@ -100,7 +100,7 @@ int plan(faco_batch* b, int m) {
     for (int i = 0; i < C; ++i) b->variant[i] = b->plan_mode;
   }
   for (int i = 0; i < C; ++i)
-    if (b->a.cap[i] <= 0) b->variant[i] = 1;
+    if (b->a.cap[i] <= 0 && b->variant[i] == kVarTable) b->variant[i] = kVarArr2;
   int rc = antset_zero(b->a, b->stream);  // counters written by trial launches
   if (rc != FACO_OK) return rc;
   rc = b->r.build(entries_of(b), b->smem_blk, b->stream);
@@ -269,7 +269,7 @@ int faco_batch_stats(faco_batch* b, int32_t i, faco_stats* s) {
     }
   }
   s->kernel_launches = b->launches;
-  s->seg_cap = (b->variant.empty() || b->variant[i] != 0) ? 0 : (b->a.m > 0 ? b->a.cap[i] : 0);
+  s->seg_cap = (b->variant.empty() || b->variant[i] != kVarTable) ? 0 : (b->a.m > 0 ? b->a.cap[i] : 0);
   return FACO_OK;
 }
 
@@ -282,7 +282,7 @@ int faco_batch_tau(faco_batch* b, int32_t i, float* tau) {
 }
 
 int faco_batch_set_plan(faco_batch* b, int32_t mode) {
-  if (!b || mode < -1 || mode > 1) return FACO_E_ARG;
+  if (!b || mode < -1 || mode >= kNVariants) return FACO_E_ARG;
   if (mode != b->plan_mode) {
     b->plan_mode = mode;
     b->planned = false;

@@ -14,11 +14,27 @@ cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr);
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs);
 cudaError_t launch_ants_blk_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int blocks,
                                   int2* redo_list, int32_t* redo_n, size_t smem, cudaStream_t s);
-cudaError_t launch_ants_arr_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int nmap,
+// batch array kernel: minb = 2, 4 or 8 blocks per SM (registers per thread
+// 255, 128, 64); one translation unit per bound (ants_arr_bMB.cu)
+cudaError_t launch_ants_arr_batch(int kw, int minb, const Colony* cols, const Ants* ants, const int2* map, int nmap,
                                   int redo_blocks, const int2* redo_list, const int32_t* redo_n,
                                   size_t per_warp, cudaStream_t s);
+#define FACO_ARR_B_DECL(MB)                                                                                   \
+  cudaError_t launch_ants_arr_batch_##MB(int kw, const Colony* cols, const Ants* ants, const int2* map,       \
+                                         int nmap, int redo_blocks, const int2* redo_list,                    \
+                                         const int32_t* redo_n, size_t per_warp, cudaStream_t s);             \
+  cudaError_t prepare_ants_arr_batch_##MB(int kw, size_t smem);                                                \
+  int occupancy_ants_arr_batch_##MB(int kw, size_t smem);
+FACO_ARR_B_DECL(2)
+FACO_ARR_B_DECL(4)
+FACO_ARR_B_DECL(8)
+#undef FACO_ARR_B_DECL
 cudaError_t prepare_ants_batch(int kw, size_t smem_blk, size_t smem_arr);
 size_t ants_blk_batch_smem(int kw);
+// Ants resident per SM for a batch per-ant kernel: variant 0 = segment-table
+// block (smem = its dynamic shared memory), 1..3 = array kernel with 2, 4, 8
+// blocks per SM (smem = four warps' visited bits).
+int ants_batch_resident(int variant, int kw, size_t smem);
 
 // colony.cu
 cudaError_t launch_rows(const Colony& C, int update, cudaStream_t s);

@@ -288,6 +288,11 @@ int antset_zero(const AntSet& a, cudaStream_t s) {
 // ---------------------------------------------------------------------
 Runner::~Runner() {
   if (mem) cudaFree(mem);
+  for (int v = 0; v < kNVariants; ++v) {
+    if (side[v]) cudaStreamDestroy(side[v]);
+    if (join[v]) cudaEventDestroy(join[v]);
+  }
+  if (fork) cudaEventDestroy(fork);
 }
 
 int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s) {
@@ -304,7 +309,7 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
     const RunEntry& e = entries[j];
     if (e.g->kw != kw) return FACO_E_ARG;
     Ants A = e.a->hA[e.i];
-    if (e.variant != 0 || A.seg_cap <= 0) {
+    if (e.variant != kVarTable || A.seg_cap <= 0) {
       A.seg_cap = 0;
       A.segs = nullptr;
       A.nseg = nullptr;
@@ -320,26 +325,28 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return entries[x].g->n[entries[x].i] > entries[y].g->n[entries[y].i];
   });
-  std::vector<int2> mblk, marr, m256;
+  std::vector<int2> mblk, marr[kNVariants], m256;
   for (int j : order) {
     const int m = hA[j].m;
     if (hA[j].segs) {
       for (int a = 0; a < m; ++a) mblk.push_back(make_int2(j, a));
     } else {
-      for (int a = 0; a < m; a += 4) marr.push_back(make_int2(j, a));
+      int v = entries[j].variant;
+      if (v < kVarArr2 || v >= kNVariants) v = kVarArr2;
+      for (int a = 0; a < m; a += 4) marr[v].push_back(make_int2(j, a));
     }
   }
   for (int j = 0; j < C; ++j) add_blocks(m256, j, entries[j].g->n[entries[j].i], 256);
   nblk = (int)mblk.size();
-  narr = (int)marr.size();
+  for (int v = 0; v < kNVariants; ++v) narr[v] = (int)marr[v].size();
   nmap256 = (int)m256.size();
-  redo_blocks = nblk > 0 ? kRedoBlocks : 0;
+  redo_blocks = nblk > 0 ? kRedoBlocks : 0;  // a launch of its own, after the segment-table launch
   // one device block: tables, maps, redo list and count
   Bump B(nullptr);
   B.take<Colony>(C);
   B.take<Ants>(C);
   B.take<int2>(mblk.size());
-  B.take<int2>(marr.size());
+  for (int v = 0; v < kNVariants; ++v) B.take<int2>(marr[v].size());
   B.take<int2>(m256.size());
   B.take<int2>((size_t)redo_cap);
   B.take<int32_t>(1);
@@ -357,7 +364,7 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
   dC = D.take<Colony>(C);
   dA = D.take<Ants>(C);
   map_blk = D.take<int2>(mblk.size());
-  map_arr = D.take<int2>(marr.size());
+  for (int v = 0; v < kNVariants; ++v) map_arr[v] = D.take<int2>(marr[v].size());
   map256 = D.take<int2>(m256.size());
   redo_list = D.take<int2>((size_t)redo_cap);
   redo_n = D.take<int32_t>(1);
@@ -373,25 +380,54 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
   CK(cudaMemcpyAsync(dA, hA.data(), sizeof(Ants) * C, cudaMemcpyHostToDevice, s));
   if (!mblk.empty())
     CK(cudaMemcpyAsync(map_blk, mblk.data(), sizeof(int2) * mblk.size(), cudaMemcpyHostToDevice, s));
-  if (!marr.empty())
-    CK(cudaMemcpyAsync(map_arr, marr.data(), sizeof(int2) * marr.size(), cudaMemcpyHostToDevice, s));
+  for (int v = 0; v < kNVariants; ++v)
+    if (!marr[v].empty())
+      CK(cudaMemcpyAsync(map_arr[v], marr[v].data(), sizeof(int2) * marr[v].size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(map256, m256.data(), sizeof(int2) * m256.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(redo_n, 0, sizeof(int32_t), s));
   CK(prepare_ants_batch(kw, smem_blk, 4 * per_warp));
+  if (!fork) {
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int v = 0; v < kNVariants; ++v) {
+      CK(cudaStreamCreateWithFlags(&side[v], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&join[v], cudaEventDisableTiming));
+    }
+  }
   return FACO_OK;
 }
 
 int Runner::enqueue(cudaStream_t s, int parts) const {
   if (parts & 1) {
-    CK(launch_ants_blk_batch(kw, dC, dA, map_blk, nblk, redo_list, redo_n, smem_blk, s));
-    CK(launch_ants_arr_batch(kw, dC, dA, map_arr, narr, redo_blocks, redo_list, redo_n, per_warp, s));
+    // every per-ant launch on its own branch; the redo list after the
+    // segment-table launch that fills it
+    int used[kNVariants];
+    int nused = 0;
+    for (int v = 0; v < kNVariants; ++v)
+      if (v == kVarTable ? nblk > 0 : narr[v] > 0) used[nused++] = v;
+    if (nused > 1) CK(cudaEventRecord(fork, s));
+    for (int u = 0; u < nused; ++u) {
+      const int v = used[u];
+      cudaStream_t q = u == 0 ? s : side[v];
+      if (u > 0) CK(cudaStreamWaitEvent(q, fork, 0));
+      if (v == kVarTable) {
+        CK(launch_ants_blk_batch(kw, dC, dA, map_blk, nblk, redo_list, redo_n, smem_blk, q));
+        CK(launch_ants_arr_batch(kw, 2, dC, dA, nullptr, 0, redo_blocks, redo_list, redo_n, per_warp, q));
+      } else {
+        CK(launch_ants_arr_batch(kw, kArrMinBlocks[v], dC, dA, map_arr[v], narr[v], 0, redo_list, redo_n,
+                                 per_warp, q));
+      }
+      if (u > 0) CK(cudaEventRecord(join[v], q));
+    }
+    for (int u = 1; u < nused; ++u) CK(cudaStreamWaitEvent(s, join[used[u]], 0));
   }
   if (parts & 2) CK(launch_colony_update_batch(dC, dA, count, map256, nmap256, redo_n, s));
   return FACO_OK;
 }
 
 int Runner::kernels_per_iteration() const {
-  return (nblk > 0 ? 1 : 0) + (narr + redo_blocks > 0 ? 1 : 0) + 5;
+  int k = (nblk > 0 ? 2 : 0) + 5;
+  for (int v = kVarArr2; v < kNVariants; ++v) k += narr[v] > 0;
+  return k;
 }
 
 // ---------------------------------------------------------------------
@@ -426,14 +462,21 @@ void tuner_put(int cls, int m, int kw, int variant) {
 }
 
 int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s) {
-  // the untuned classes, and up to 64 colonies of each
+  // the untuned classes, and up to 64 colonies of each (spread over the
+  // class when it has more)
   std::map<std::pair<int, int>, std::vector<RunEntry>> cls;
   for (const RunEntry& e : entries) {
     const int c = size_class(e.g->n[e.i]);
     const int m = e.a->m;
     if (tuner_get(c, m, e.g->kw) >= 0) continue;
-    auto& v = cls[std::make_pair(c, m)];
-    if (v.size() < 64) v.push_back(e);
+    cls[std::make_pair(c, m)].push_back(e);
+  }
+  for (auto& kv : cls) {
+    std::vector<RunEntry>& v = kv.second;
+    if (v.size() <= 64) continue;
+    std::vector<RunEntry> pick;
+    for (int j = 0; j < 64; ++j) pick.push_back(v[(size_t)j * v.size() / 64]);
+    v.swap(pick);
   }
   if (cls.empty()) return FACO_OK;
   cudaEvent_t ev[2];
@@ -444,14 +487,18 @@ int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s)
     CK(ce);
   }
   int rc = FACO_OK;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur_device());
   for (auto& kv : cls) {
     std::vector<RunEntry>& v = kv.second;
     bool any_tab = false;
     for (const RunEntry& e : v) any_tab |= e.a->cap[e.i] > 0;
-    int best = 1;
-    if (any_tab) {
-      float t[2] = {0, 0};
-      for (int variant = 0; variant < 2 && rc == FACO_OK; ++variant) {
+    int best = kVarArr2;
+    {
+      float t[kNVariants];
+      for (int variant = 0; variant < kNVariants && rc == FACO_OK; ++variant) {
+        t[variant] = 1e30f;
+        if (variant == kVarTable && !any_tab) continue;
         for (RunEntry& e : v) e.variant = variant;
         Runner r;
         rc = r.build(v, smem, s);
@@ -466,10 +513,20 @@ int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s)
           tmin = std::min(tmin, ms);
         }
         if (rc == FACO_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FACO_E_CUDA;
-        t[variant] = tmin;
+        // A class that does not fill the GPU's resident ant slots leaves the
+        // rest to the other classes of a batch: its cost there is the time
+        // measured alone times the fraction of slots it holds.
+        int ants = 0;
+        for (const RunEntry& e : v) ants += e.a->m;
+        const int per_sm = ants_batch_resident(variant, v[0].g->kw,
+                                               variant == kVarTable ? r.smem_blk : 4 * r.per_warp);
+        const double slots = (double)per_sm * sms;
+        const double frac = slots > 0 ? std::min(1.0, ants / slots) : 1.0;
+        t[variant] = (float)(tmin * frac);
       }
       if (rc != FACO_OK) break;
-      best = t[0] <= t[1] ? 0 : 1;
+      for (int variant = 0; variant < kNVariants; ++variant)
+        if (t[variant] < t[best]) best = variant;
     }
     tuner_put(kv.first.first, kv.first.second, v[0].g->kw, best);
   }

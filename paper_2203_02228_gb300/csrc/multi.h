@@ -74,18 +74,32 @@ struct RunEntry {
   const Group* g;
   int i;                        // colony within g
   const AntSet* a;
-  int variant;                  // 0 segment-table block, 1 arrays
+  int variant;                  // kVariant*
 };
 
+// Per-ant kernel of a colony: a block of four warps per ant on a segment
+// table, or one warp per ant on explicit arrays with the kernel compiled for
+// 2, 4 or 8 resident blocks per SM.
+enum : int { kVarTable = 0, kVarArr2 = 1, kVarArr4 = 2, kVarArr8 = 3, kNVariants = 4 };
+constexpr int kArrMinBlocks[kNVariants] = {0, 2, 4, 8};
+
 struct Runner {
-  int count = 0, kw = 16, nblk = 0, narr = 0, nmap256 = 0, redo_blocks = 0;
+  int count = 0, kw = 16, nblk = 0, nmap256 = 0, redo_blocks = 0;
+  int narr[kNVariants] = {0, 0, 0, 0};
   size_t smem_blk = 0, per_warp = 0;
   char* mem = nullptr;          // one cudaMalloc: tables, maps, redo list
   size_t mem_bytes = 0;
   Colony* dC = nullptr;
   Ants* dA = nullptr;
-  int2 *map_blk = nullptr, *map_arr = nullptr, *map256 = nullptr, *redo_list = nullptr;
+  int2* map_arr[kNVariants] = {nullptr, nullptr, nullptr, nullptr};
+  int2 *map_blk = nullptr, *map256 = nullptr, *redo_list = nullptr;
   int32_t* redo_n = nullptr;
+  // the per-ant launches of different kernels run side by side: forked from
+  // and joined back into the caller's stream with events (graph branches
+  // when captured)
+  cudaStream_t side[kNVariants] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kNVariants] = {nullptr, nullptr, nullptr, nullptr};
   ~Runner();
   // Builds tables and maps for `entries` (enqueued on s).
   int build(const std::vector<RunEntry>& entries, size_t smem_blk, cudaStream_t s);

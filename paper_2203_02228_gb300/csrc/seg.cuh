@@ -175,7 +175,7 @@ __device__ __forceinline__ void del2(uint16_t* ids, int32_t* keys, uint16_t* ran
 
 // Ensure a segment starts at ant position t (0 < t < n).  Keys are current
 // on entry and on exit.  false: table full.
-__device__ __noinline__ bool seg_split(const SegTab& T, int t) {
+static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
   const int S = *T.S;
   const int r = bsearch_le(T.offA, S, t);
   const int id = T.A[r];
@@ -211,7 +211,7 @@ __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
 
 // Merge ant ranks r and r+1 if the second continues the first in the
 // source (r + 1 > 0, so never across ant position 0).  Keys stay current.
-__device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
+static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   const int S = *T.S;
   if (r < 0 || r + 1 >= S) return;
   const int ia = T.A[r], ib = T.A[r + 1];
@@ -264,7 +264,7 @@ __device__ __forceinline__ void seg_free_id(const SegTab& T, int dead, int S_aft
 
 // Merge ant-adjacent segments that continue each other in the source
 // (never across ant position 0).  Keys are rebuilt.
-__device__ __noinline__ void seg_merge_all(const SegTab& T) {
+static __device__ __noinline__ void seg_merge_all(const SegTab& T) {
   const int lane = lane_id();
   for (;;) {
     const int S = *T.S;

@@ -38,7 +38,7 @@ ALGO_COUNTERS = ("iteration", "best_length", "initial_length", "source_length", 
                  "backup_picks", "global_picks", "ls_pops", "moves_2opt", "moves_or")
 
 
-@pytest.mark.parametrize("plan", [None, 0, 1], ids=["tuned", "tables", "arrays"])
+@pytest.mark.parametrize("plan", [None, 0, 1, 2, 3], ids=["tuned", "tables", "arrays2", "arrays4", "arrays8"])
 def test_batch_equals_single_colonies(plan):
     xs = mixed_instances()
     seeds = (np.arange(len(xs), dtype=np.uint64) * 7919 + 3)
@@ -68,7 +68,7 @@ def test_batch_plans_agree_and_match_oracle():
     xs = mixed_instances()[:6]
     seeds = np.arange(11, 17, dtype=np.uint64)
     res = []
-    for plan in (0, 1, -1):
+    for plan in (0, 1, 3, -1):
         b = Batch(xs, 16, seeds=seeds, plan=plan)
         b.iterate(10, 6)
         res.append((b.tours(), [b.tau(i) for i in range(len(xs))]))
