@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib
 from ._lib import FacoError, faco_params, faco_stats, load, params_default  # noqa: F401
 
-__all__ = ["Batch", "Colony", "FacoError", "faco_params", "faco_stats", "load", "params_default",
+__all__ = ["Batch", "Colony", "FacoError", "Server", "faco_params", "faco_stats", "load", "params_default",
            "faco_create", "faco_create_ex", "faco_create_device", "faco_iterate", "faco_sync",
            "faco_best", "faco_best_device", "faco_stats_get", "faco_destroy", "faco_strerror"]
 
@@ -312,6 +312,82 @@ class Batch:
         v = np.empty(self.count, np.int32)
         _lib.check(self._L.faco_batch_get_plan(self._h, _ptr(v)), "faco_batch_get_plan")
         return v
+
+
+class Server:
+    """Request server (include/faco_serve.h): instances admitted by device
+    memory, set up while others iterate, iterated in shared rounds.
+
+    A request's tour and length equal those of a Colony with the server's
+    parameters and the request's seed, alone or in any mix.
+    """
+
+    def __init__(self, device_bytes: int, params: faco_params | None = None, **kw):
+        p = params if params is not None else params_default()
+        for key, v in kw.items():
+            setattr(p, key, v)
+        self.params = p
+        self._L = load()
+        h = ctypes.c_void_p()
+        _lib.check(self._L.faco_server_create(int(device_bytes), ctypes.byref(p), ctypes.byref(h)),
+                   "faco_server_create")
+        self._h = h
+        self._n = {}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.faco_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def request_bytes(self, n: int, k: int, ants: int) -> int:
+        return int(self._L.faco_server_request_bytes(n, k, ants, ctypes.byref(self.params)))
+
+    def submit(self, coords, k: int, ants: int, budget: int, seed: int) -> int:
+        xy = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 2)
+        t = ctypes.c_uint64()
+        _lib.check(self._L.faco_server_submit(self._h, _ptr(xy), xy.shape[0], k, ants, budget, seed,
+                                              ctypes.byref(t)), "faco_server_submit")
+        self._n[t.value] = xy.shape[0]
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """None while pending, else (tour, length, t_submit_ns, t_done_ns)."""
+        n = self._n.get(ticket, 0)  # unknown tickets: the library reports FACO_E_ARG
+        tour = np.empty(n, np.int32)
+        L, ts, td = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        rc = self._L.faco_server_poll(self._h, ticket, _ptr(tour), n, ctypes.byref(L), ctypes.byref(ts),
+                                      ctypes.byref(td))
+        if rc == _lib.FACO_PENDING:
+            return None
+        _lib.check(rc, "faco_server_poll")
+        return tour, int(L.value), int(ts.value), int(td.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        rc = self._L.faco_server_wait(self._h, ticket, timeout_ms)
+        if rc == _lib.FACO_PENDING:
+            raise TimeoutError("request %d still pending after %d ms" % (ticket, timeout_ms))
+        return self.poll(ticket)
+
+    def release(self, ticket: int) -> None:
+        _lib.check(self._L.faco_server_release(self._h, ticket), "faco_server_release")
+        self._n.pop(ticket, None)
+
+    def stats(self):
+        st = _lib.faco_server_stats()
+        _lib.check(self._L.faco_server_stats_get(self._h, ctypes.byref(st)), "faco_server_stats_get")
+        return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 def device_selftest(what: int, inp: np.ndarray, out: np.ndarray, count: int, width: int = 16, seed: int = 0) -> None:

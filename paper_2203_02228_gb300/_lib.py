@@ -67,6 +67,15 @@ class faco_stats(ctypes.Structure):
     ]
 
 
+class faco_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "submitted", "completed", "queued", "setting_up", "active", "peak_active", "rounds",
+        "kernel_launches", "pool_bytes", "pool_in_use")]
+
+
+FACO_PENDING = 1
+
+
 class FacoError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -127,6 +136,16 @@ def load():
             "faco_batch_set_plan": (ctypes.c_int, [vp, i32]),
             "faco_batch_get_plan": (ctypes.c_int, [vp, vp]),
             "faco_batch_destroy": (None, [vp]),
+            # include/faco_serve.h
+            "faco_server_create": (ctypes.c_int, [ctypes.c_size_t, P(faco_params), P(vp)]),
+            "faco_server_request_bytes": (i64, [i32, i32, i32, P(faco_params)]),
+            "faco_server_submit": (ctypes.c_int, [vp, vp, i32, i32, i32, i32, ctypes.c_uint64,
+                                                  P(ctypes.c_uint64)]),
+            "faco_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, i32, P(i64), P(i64), P(i64)]),
+            "faco_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, i32]),
+            "faco_server_release": (ctypes.c_int, [vp, ctypes.c_uint64]),
+            "faco_server_stats_get": (ctypes.c_int, [vp, P(faco_server_stats)]),
+            "faco_server_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -130,3 +130,19 @@ def test_batch_no_cpu_fallback_without_gpu(lib):
     h = ctypes.c_void_p()
     rc = lib.faco_batch_create(ptrs, ns.ctypes.data_as(ctypes.c_void_p), 2, 16, None, None, ctypes.byref(h))
     assert rc == _lib.FACO_E_CUDA
+
+
+def test_server_without_gpu_and_request_sizes(lib):
+    import torch
+
+    b1 = lib.faco_server_request_bytes(1000, 16, 8, None)
+    b2 = lib.faco_server_request_bytes(2000, 16, 8, None)
+    b3 = lib.faco_server_request_bytes(1000, 16, 64, None)
+    assert 0 < b1 < b2 and b1 < b3
+    # per-ant buffers: at least route, pos, checklist, queue, log (int32) and flags per node and ant
+    assert b3 - b1 >= (64 - 8) * 1000 * 21
+    assert lib.faco_server_request_bytes(1000, 16, 0, None) == -1
+    assert lib.faco_server_create(1 << 20, None, None) == _lib.FACO_E_ARG
+    if not torch.cuda.is_available():
+        h = ctypes.c_void_p()
+        assert lib.faco_server_create(1 << 20, None, ctypes.byref(h)) == _lib.FACO_E_CUDA
