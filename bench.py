@@ -265,6 +265,74 @@ def bench_batched(args, stream, flush, barrier):
     }
 
 
+def bench_served(args, stream, barrier):
+    """A Poisson stream of requests (n log-uniform in [1e3, 1e5], 256 ants,
+    50 iterations) through the server -- admission by device memory,
+    continuous batching -- and the same arrival trace through the plain
+    loop (one Colony at a time, first come first served).  Time-to-budget
+    = completion - arrival, host clock."""
+    import threading as th
+
+    from paper_2203_02228_gb300 import Colony, Server, inputs
+
+    w = inputs.SERVE_WORKLOADS["serve100k"]
+    out = {"workload": "serve100k", "ants": w["ants"], "iterations": w["iters"], "k": w["k"],
+           "n_range": [w["lo"], w["hi"]], "metric": "time-to-budget p50/p99 (s), instances/sec",
+           "pool_bytes": args.serve_pool_gb << 30, "rates": []}
+    # warm: kernel tuner and module load, outside the timed streams
+    with Server(1 << 30) as s:
+        for j, n in enumerate((1500, 6000, 30000)):
+            s.wait(s.submit(inputs.uniform(n, seed=j), w["k"], w["ants"], 2, 1))
+    for rate in args.serve_rates:
+        xs, seeds, arr = inputs.serve_trace("serve100k", args.serve_requests, rate)
+        # served
+        barrier()
+        with Server(args.serve_pool_gb << 30) as s:
+            t0 = time.perf_counter()
+            tickets = [None] * len(xs)
+
+            def feed():
+                for i, x in enumerate(xs):
+                    d = t0 + arr[i] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    tickets[i] = s.submit(x, w["k"], w["ants"], w["iters"], int(seeds[i]))
+
+            f = th.Thread(target=feed)
+            f.start()
+            f.join()
+            res = [s.wait(t) for t in tickets]
+            st = s.stats()
+        lat = np.array([(r[3] - r[2]) / 1e9 for r in res])
+        span = (max(r[3] for r in res) - min(r[2] for r in res)) / 1e9
+        served = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                  "mean_s": float(lat.mean()), "instances_per_s": len(xs) / span,
+                  "ant_solutions_per_s": len(xs) * w["ants"] * w["iters"] / span,
+                  "peak_active": st["peak_active"], "rounds": st["rounds"],
+                  "gpu_launches": st["kernel_launches"], "mean_best_length": float(np.mean([r[1] for r in res]))}
+        # plain loop, same trace: one instance at a time in arrival order
+        barrier()
+        t0 = time.perf_counter()
+        plat, plens = [], []
+        for i, x in enumerate(xs):
+            d = t0 + arr[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            c = Colony(x, w["k"], seed=int(seeds[i]), stream=stream)
+            c.iterate(w["ants"], w["iters"])
+            tour, L = c.best()
+            c.close()
+            plat.append(time.perf_counter() - (t0 + arr[i]))
+            plens.append(L)
+        pspan = time.perf_counter() - t0
+        plat = np.array(plat)
+        plain = {"p50_s": float(np.percentile(plat, 50)), "p99_s": float(np.percentile(plat, 99)),
+                 "mean_s": float(plat.mean()), "instances_per_s": len(xs) / pspan}
+        out["rates"].append({"rate_per_s": rate, "requests": len(xs), "served": served, "plain_loop": plain,
+                             "equal_lengths": bool(np.array_equal([r[1] for r in res], plens))})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,8 +344,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-ants", type=int, default=32)
     ap.add_argument("--iters", type=int, default=0, help="override the iteration budget (testing only)")
-    ap.add_argument("--sections", default="main,batch", help="comma list of: main, batch")
+    ap.add_argument("--sections", default="main,batch,serve", help="comma list of: main, batch, serve")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2.0])
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-pool-gb", type=int, default=64)
     args = ap.parse_args()
     sections = set(args.sections.split(","))
 
@@ -331,6 +402,8 @@ def main():
         out = {}
         if "batch" in sections:
             out["batched"] = bench_batched(args, stream, flush, barrier)
+        if "serve" in sections:
+            out["served"] = bench_served(args, stream, barrier)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
@@ -415,9 +488,11 @@ def main():
                "sample": "oracle set-up of the full instance (%.1f s) + 1 iteration of 32 ants (%.1f ms per "
                          "ant-solution), extrapolated to %d ants x %d iterations" % (tc, ti * 1e3, ants, iters)}
 
-    batched = None
+    batched = served = None
     if "batch" in sections and world == 1:
         batched = bench_batched(args, stream, flush, barrier)
+    if "serve" in sections and world == 1:
+        served = bench_served(args, stream, barrier)
 
     if rank == 0:
         line = {
@@ -428,7 +503,7 @@ def main():
                        "seed": 1, "l2": "flushed before every step (512 MB write)",
                        "parallelism": "independent colonies per rank" if world > 1 else "single colony"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clk, "batched": batched,
+            "clocks": clk, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

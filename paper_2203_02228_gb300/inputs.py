@@ -144,6 +144,23 @@ BATCH_WORKLOADS = {
 }
 
 
+# The served workload: a Poisson stream of uniform instances with log-uniform
+# sizes; request i uses Philox seed seed0 + i.
+SERVE_WORKLOADS = {
+    "serve100k": dict(seed=5000, lo=1_000, hi=100_000, side=1_000_000, k=16, ants=256, iters=50, seed0=1),
+}
+
+
+def serve_trace(name: str, count: int, rate: float, seed: int = 0):
+    """(instances, seeds, arrival offsets in seconds) of `count` requests of a
+    served workload arriving as a Poisson process of `rate` per second."""
+    w = SERVE_WORKLOADS[name]
+    xs = batch_instances(count, w["seed"] + seed, w["lo"], w["hi"], w["side"])
+    gaps = _rng(w["seed"] + 7919 + seed).exponential(1.0 / rate, count)
+    gaps[0] = 0.0
+    return xs, np.arange(w["seed0"], w["seed0"] + count, dtype=np.uint64), np.cumsum(gaps)
+
+
 def batch_workload(name: str):
     """(instances, seeds) of a batched workload."""
     w = BATCH_WORKLOADS[name]
