@@ -21,6 +21,17 @@ L2 is flushed (a 512 MB write) before every timed step.  Under torchrun each
 rank solves its own copy of the instance (independent colonies, no data-path
 collective): weak scaling.
 
+Two more sections ride on the same line (both on by default, --sections):
+  batched   512 independent instances (n log-uniform in [200, 20,000], 64
+            ants, 100 iterations) as one Batch -- one graph launch for the
+            budget -- vs. the plain one-Colony-at-a-time loop on a
+            stratified sample of the same instances (instances/s);
+  served    a Poisson stream of requests (n log-uniform in [1,000,
+            100,000], 256 ants, 50 iterations) through the Server vs. the
+            plain loop on the same trace (p50/p99 time-to-budget,
+            instances/s).
+Each carries its own oracle timing on a bounded sample.
+
 --impl reference times the CPU oracle instead (the method's plain
 statement, test infrastructure) on a bounded sample of the same workload.
 """
@@ -115,7 +126,7 @@ def host_cores() -> int:
 
 # Sources of the per-ant kernel; the DRAM traffic recorded under profiles/
 # applies only while their hash matches the one recorded with it.
-ANTS_SOURCES = ["ants.cu", "ls.cuh", "seg.cuh", "nearest.cuh", "common.cuh"]
+ANTS_SOURCES = ["ants.cuh", "ants_blk_body.inc", "ls.cuh", "seg.cuh", "nearest.cuh", "common.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_ants_blk_stippled100k_traffic.json")
 
 
@@ -247,6 +258,26 @@ def bench_batched(args, stream, flush, barrier):
     same = all(np.array_equal(plain[i][0], tours[i]) and plain[i][1] == lens[i] for i in plain)
     inst_batch = len(xs) / t_batch
     inst_plain = len(sample) / t_plain
+    cpu = None
+    if not args.no_cpu:
+        # the oracle on 8 instances spread over the sizes: set-up + 1 iteration
+        # of the 64 ants, extrapolated to 100 iterations; instances/s of the
+        # whole batch = 512 / (64 x the sample's time)
+        import oracle
+
+        osample = order[32::64]
+        t_sum = 0.0
+        for i in osample:
+            t0 = time.perf_counter()
+            col = oracle.Colony(xs[int(i)], k, seed=int(seeds[i]), threads=host_cores())
+            t1 = time.perf_counter()
+            col.iterate(ants, 1)
+            t2 = time.perf_counter()
+            col.close()
+            t_sum += (t1 - t0) + iters * (t2 - t1)
+        cpu = {"value": len(osample) / t_sum, "unit": "instances/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "%d of %d instances (every 64th by size): oracle set-up + 1 iteration of %d ants, "
+                         "extrapolated to %d iterations" % (len(osample), len(xs), ants, iters)}
     return {
         "workload": "batch512", "instances": len(xs), "n_range": [int(ns.min()), int(ns.max())],
         "n_mean": float(ns.mean()), "ants": ants, "iterations": iters, "k": k,
@@ -260,7 +291,7 @@ def bench_batched(args, stream, flush, barrier):
         "equal_results_on_sample": bool(same),
         "mean_best_length": float(np.mean(lens)),
         "plan": {"segment_table_colonies": int((plan == 0).sum()), "array_colonies": int((plan == 1).sum())},
-        "gpu_launches_per_batch": int(launches), "graph_launches_per_batch": 1,
+        "gpu_launches_per_batch": int(launches), "graph_launches_per_batch": 1, "cpu_baseline": cpu,
         "h2d_bytes_per_batch": int(8 * ns.sum()), "d2h_bytes_per_batch": int(4 * ns.sum() + 8 * len(xs)),
     }
 
@@ -330,6 +361,28 @@ def bench_served(args, stream, barrier):
                  "mean_s": float(plat.mean()), "instances_per_s": len(xs) / pspan}
         out["rates"].append({"rate_per_s": rate, "requests": len(xs), "served": served, "plain_loop": plain,
                              "equal_lengths": bool(np.array_equal([r[1] for r in res], plens))})
+    if not args.no_cpu:
+        # the oracle on three requests of the trace (10th, 50th, 90th size
+        # percentile): set-up + 1 iteration of 32 ants, scaled to 256 ants x 50
+        import oracle
+
+        xs, seeds, _ = inputs.serve_trace("serve100k", args.serve_requests, args.serve_rates[0])
+        ns = np.array([x.shape[0] for x in xs])
+        order = np.argsort(ns)
+        pick = [order[int(q * (len(xs) - 1))] for q in (0.1, 0.5, 0.9)]
+        t_sum = 0.0
+        for i in pick:
+            t0 = time.perf_counter()
+            col = oracle.Colony(xs[int(i)], w["k"], seed=int(seeds[i]), threads=host_cores())
+            t1 = time.perf_counter()
+            col.iterate(32, 1)
+            t2 = time.perf_counter()
+            col.close()
+            t_sum += (t1 - t0) + w["iters"] * (t2 - t1) * w["ants"] / 32
+        out["cpu_baseline"] = {"value": len(pick) / t_sum, "unit": "instances/s", "cores": host_cores(),
+                               "kind": "oracle", "sample": "3 requests (10th/50th/90th size percentile, n = %s): "
+                               "oracle set-up + 1 iteration of 32 ants, scaled to %d ants x %d iterations; one "
+                               "request at a time" % ([int(ns[i]) for i in pick], w["ants"], w["iters"])}
     return out
 
 

@@ -560,107 +560,6 @@ __device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
   A.stats[(size_t)ant * kNStats + kStRedo] += 1;
 }
 
-// Segment-table kernel body: the whole block runs ant `ant`.  Returns true
-// (in every thread) when the table filled up during construction and the
-// ant is left to the array kernel.
-template <int KW>
-__device__ __forceinline__ bool ants_blk_body(const Colony& C, const Ants& A, int ant) {
-  extern __shared__ __align__(16) char smem[];
-  __shared__ LsShared sh;
-  __shared__ int s_nchk, s_overflow;
-  __shared__ int64_t s_pre_len;
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int n = C.n;
-  const int words = (n + 31) >> 5;
-  const size_t vis_bytes = ((size_t)words * 4 + 15) & ~(size_t)15;
-  uint32_t* vis = reinterpret_cast<uint32_t*>(smem);
-  const SegTab tab = segtab_at(smem + vis_bytes, A.seg_cap);
-  const uint32_t iter = (uint32_t)(C.st->iter + 1);
-  const uint64_t t_start = global_ns();
-  int32_t* route = A.route + (size_t)ant * n;
-  int32_t* chk = A.chk + (size_t)ant * n;
-
-  Walk W;
-  W.segs = true;
-  W.tab = tab;
-  W.fall_ns = 0;
-  W.aco = W.backup = W.global = 0;
-  W.new_edges = W.nchk = 0;
-  uint64_t t_cons = t_start;
-  if (w == 0) {
-    if (lane == 0) *tab.S = 0;
-    __syncwarp();
-    const int64_t pre_len = construct<KW>(C, nullptr, nullptr, vis, chk, W, (uint32_t)ant, iter);
-    t_cons = global_ns();
-    if (!W.overflow) seg_finish_construction(tab);
-    if (lane == 0) {
-      s_pre_len = pre_len;
-      s_nchk = W.nchk;
-      s_overflow = W.overflow;
-    }
-    if (!W.overflow && A.pre_route) {
-      seg_materialize(C, tab, A.pre_route + (size_t)ant * n);
-      for (int i = lane; i < W.nchk; i += 32) A.pre_chk[(size_t)ant * n + i] = C.src_route[chk[i]];
-      if (lane == 0) {
-        A.pre_len[ant] = pre_len;
-        A.pre_nchk[ant] = W.nchk;
-      }
-    }
-  }
-  __syncthreads();
-  if (s_overflow) {
-    if (tid == 0) A.redo[ant] = 1;
-    return true;
-  }
-  LsEnv E{n, C.oropt, C.verify, A.queue + (size_t)ant * n, A.flags + (size_t)ant * n,
-          A.logb + (size_t)ant * n};
-  LsStats S{0, 0, 0, 0, 0};
-  __shared__ int32_t s_mode;
-  if (tid == 0) s_mode = 0;
-  __syncthreads();
-  HybTour T{n, C.k, SegTour{n, C.k, C.kw, tab, C.XYsrc, C.Csrc},
-            ArrTour{n, C.k, route, A.pos + (size_t)ant * n, C.XYsrc, C.Csrc, C.kw}, &s_mode};
-  const int64_t gain = ls_run_block(E, T, chk, s_nchk, S, sh);
-  // hand the tour over: segments in ant order, or arrays of source positions
-  // (-2) when the table filled up; arrays of node ids (-1) for inspection
-  int Sn;
-  if (!s_mode) {
-    Sn = *tab.S;
-    int4* out = A.segs + (size_t)ant * A.seg_cap;
-    for (int r = tid; r < Sn; r += blockDim.x) {
-      const Seg s = tab.sg[tab.A[r]];
-      out[r] = make_int4(s.lo, s.len, s.off, s.rev);
-    }
-    if (w == 0 && A.keep_tours) seg_materialize(C, tab, route);
-  } else {
-    Sn = -2;
-    if (A.keep_tours) {
-      Sn = -1;
-      for (int t = tid; t < n; t += blockDim.x) route[t] = C.src_route[route[t]];
-    }
-  }
-  if (tid == 0) {
-    if (s_mode) st_redo_add(A, ant);
-    A.nseg[ant] = Sn;
-    A.len[ant] = s_pre_len - gain;
-    A.redo[ant] = 0;
-    int64_t* st = A.stats + (size_t)ant * kNStats;
-    // counters accumulate over iterations (zeroed when the ant buffers are made)
-    st[kStAco] += W.aco; st[kStNew] += W.new_edges; st[kStBackup] += W.backup;
-    st[kStGlobal] += W.global; st[kStCheck] += W.nchk; st[kStPops] += S.pops;
-    st[kStMoves2] += S.moves2; st[kStMovesOr] += S.movesor; st[kStFlip] += S.flip;
-    st[kStVerify] += S.verify;
-    st[kStStartNs] = (int64_t)t_start;
-    st[kStDurNs] = (int64_t)(global_ns() - t_start);
-    st[kStConsNs] = (int64_t)(t_cons - t_start);
-    st[kStFallNs] = W.fall_ns;
-    st[kStEvalNs] = S.t_eval;
-    st[kStConfNs] = S.t_confirm;
-    st[kStFlipNs] = S.t_flip;
-    st[kStPushNs] = S.t_push;
-  }
-  return false;
-}
 
 // ---------------------------------------------------------------------
 // Kernels.  One colony: the Colony and Ants descriptors are kernel
@@ -680,8 +579,11 @@ __global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
 
 template <int KW>
 __global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
-  if ((int)blockIdx.x >= A.m) return;
-  (void)ants_blk_body<KW>(C, A, blockIdx.x);
+  const int ant = blockIdx.x;
+  if (ant >= A.m) return;
+#define ANTS_BLK_OVERFLOW (void)0
+#include "ants_blk_body.inc"
+#undef ANTS_BLK_OVERFLOW
 }
 
 // Copies `bytes` (a multiple of 4) with the threads lo..lo+cnt-1.
@@ -702,9 +604,14 @@ __global__ void __launch_bounds__(32 * kAntWarps, 7)
   copy_words(&sC, cols + e.x, sizeof(Colony), 0, blockDim.x);
   copy_words(&sA, ants + e.x, sizeof(Ants), 0, blockDim.x);
   __syncthreads();
-  if (e.y >= sA.m) return;
-  const bool over = ants_blk_body<KW>(sC, sA, e.y);
-  if (over && threadIdx.x == 0) redo_list[atomicAdd(redo_n, 1)] = e;
+  const Colony& C = sC;
+  const Ants& A = sA;
+  const int ant = e.y;
+  if (ant >= A.m) return;
+#define ANTS_BLK_OVERFLOW \
+  if (tid == 0) redo_list[atomicAdd(redo_n, 1)] = e
+#include "ants_blk_body.inc"
+#undef ANTS_BLK_OVERFLOW
 }
 
 // Batch, arrays: blocks below nmap run the four ants map[b].y + warp of
