@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("verify_pass", ctypes.c_int32),
         ("threads", ctypes.c_int32),
         ("keep_pre_ls", ctypes.c_int32),
+        ("local_search", ctypes.c_int32),
     ]
 
 

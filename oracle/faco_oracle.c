@@ -154,6 +154,7 @@ void orc_params_default(orc_params* p) {
   p->verify_pass = 1;
   p->threads = 1;
   p->keep_pre_ls = 0;
+  p->local_search = 1;
 }
 
 /* ------------------------------------------------------------------ */
@@ -779,10 +780,13 @@ int orc_iterate(orc_colony* C, int32_t ants, int32_t iters, int64_t* hist, int64
           C->pre_ncheck[a] = nc;
           C->pre_len[a] = orc_tour_length(C->xy, n, route);
         }
-        set_positions(n, route, pos);
         int64_t L0 = orc_tour_length(C->xy, n, route);
-        int64_t g = orc_local_search(C->xy, n, C->cand, C->k, C->prm.oropt, C->prm.verify_pass,
-                                     route, pos, check, nc, st);
+        int64_t g = 0;
+        if (C->prm.local_search) {  /* base FACO (no LS) keeps the constructed tour */
+          set_positions(n, route, pos);
+          g = orc_local_search(C->xy, n, C->cand, C->k, C->prm.oropt, C->prm.verify_pass, route, pos,
+                               check, nc, st);
+        }
         C->ant_len[a] = L0 - g;
       }
       free(visited);

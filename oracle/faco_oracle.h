@@ -30,6 +30,9 @@ typedef struct {
   int32_t verify_pass;    /* 1: re-scan visited nodes until no move is found   */
   int32_t threads;        /* OpenMP threads over ants (1 = serial)             */
   int32_t keep_pre_ls;    /* 1: keep each ant's tour before local search       */
+  int32_t local_search;   /* 1: each new tour gets the local search (FACO+LS); */
+                          /* 0: base FACO, the tour is kept as constructed     */
+                          /* (the study of min_new_edges, Figs. 1 and 3)       */
 } orc_params;
 
 typedef struct orc_colony orc_colony;

@@ -86,6 +86,7 @@ struct ArrTour {
   __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {
     const int lane = lane_id();
     int i = pos[x], j = pos[y];
+    __syncwarp();  // every lane has read i and j before a position moves
     int L = j - i;
     if (L < 0) L += n;
     L += 1;

@@ -375,6 +375,7 @@ struct SegTour {
   __device__ __noinline__ bool flip(int x, int y, LsStats& St) {
     const int lane = lane_id();
     int i = pos_of(x), j = pos_of(y);
+    __syncwarp();  // every lane has read the table before any lane rewrites a segment
     int L = j - i;
     if (L < 0) L += n;
     L += 1;

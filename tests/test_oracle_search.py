@@ -286,3 +286,34 @@ def test_limits_follow_global_best():
         assert lim[2] == np.float32(lim[0]) and lim[3] == np.float32(lim[1])
         assert 0 < lim[1] < lim[0]
         assert (C.tau() >= np.float32(lim[1])).all() and (C.tau() <= np.float32(lim[0])).all()
+
+
+def test_base_faco_keeps_constructed_tours():
+    """Base FACO (no local search on new tours; the study of min_new_edges,
+    Figs. 1 and 3): every ant's final tour is its constructed tour, so its
+    length is the constructed length; with the same seed and the same
+    source, iteration 1's tours are the pre-search tours of FACO+LS; the
+    initial tour is the same (its local search is part of the set-up)."""
+    xy = inputs.uniform(600, seed=61)
+    base = oracle.Colony(xy, 16, local_search=0, keep_pre_ls=1, min_new_edges=40, rho=0.9, threads=4)
+    ls = oracle.Colony(xy, 16, local_search=1, keep_pre_ls=1, min_new_edges=40, rho=0.9, threads=4)
+    assert base.initial()[1] == ls.initial()[1]
+    np.testing.assert_array_equal(base.initial()[0], ls.initial()[0])
+    _, base_len = base.iterate(10, 1)
+    _, ls_len = ls.iterate(10, 1)
+    bt, bl = base.ant_tours()
+    pt, pl, _ = base.ant_pre()
+    np.testing.assert_array_equal(bt, pt)
+    np.testing.assert_array_equal(bl, pl)
+    np.testing.assert_array_equal(bl, base_len[0])
+    for a in range(10):
+        assert bl[a] == oracle.tour_length(xy, bt[a])
+        assert sorted(bt[a].tolist()) == list(range(600))
+    lpt, lpl, _ = ls.ant_pre()
+    np.testing.assert_array_equal(bt, lpt)  # same construction before any search
+    assert np.all(ls_len[0] <= base_len[0]) and np.any(ls_len[0] < base_len[0])
+    # later iterations: base FACO's tours stay constructed tours
+    base.iterate(10, 4)
+    bt, bl = base.ant_tours()
+    pt, pl, _ = base.ant_pre()
+    np.testing.assert_array_equal(bt, pt)
