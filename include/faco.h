@@ -66,6 +66,11 @@ typedef struct {
                           /* ant on explicit n-entry arrays, 8..4096 = that size */
                           /* (an ant whose table fills up is redone on arrays;   */
                           /* results are identical in every case)                */
+  int32_t local_search;   /* 1: every new tour gets the local search (FACO+LS,   */
+                          /* default); 0: base FACO, tours kept as constructed   */
+                          /* (the min_new_edges study, Figs. 1 and 3, uses it    */
+                          /* with rho = 0.9); the initial tour's local search is */
+                          /* part of the set-up either way                       */
   void* stream;           /* cudaStream_t to enqueue on (NULL = own stream)       */
 } faco_params;
 

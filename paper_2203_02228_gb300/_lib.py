@@ -38,6 +38,7 @@ class faco_params(ctypes.Structure):
         ("keep_ant_tours", ctypes.c_int32),
         ("keep_pre_ls", ctypes.c_int32),
         ("seg_cap", ctypes.c_int32),
+        ("local_search", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

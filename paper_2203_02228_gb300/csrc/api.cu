@@ -99,7 +99,7 @@ Colony colony_view(const faco_ctx* c) {
   Colony C;
   C.n = c->n; C.k = c->k; C.bl = c->bl; C.kw = c->kw;
   C.seed = c->prm.seed; C.rho = c->prm.rho; C.min_new_edges = c->prm.min_new_edges;
-  C.oropt = c->prm.oropt; C.verify = c->prm.verify_pass;
+  C.oropt = c->prm.oropt; C.verify = c->prm.verify_pass; C.ls = c->prm.local_search;
   C.c_min = c->c_min; C.p_src_gb = c->prm.p_source_gb;
   C.xy = c->xy; C.cand = c->cand; C.backup = c->backup; C.eta = c->eta; C.tau = c->tau;
   C.src_route = c->src_route; C.src_pos = c->src_pos; C.gb_route = c->gb_route; C.gb_pos = c->gb_pos;
@@ -454,6 +454,7 @@ int faco_params_default(faco_params* p) {
   p->keep_ant_tours = 0;
   p->keep_pre_ls = 0;
   p->seg_cap = -1;
+  p->local_search = 1;
   p->stream = nullptr;
   return FACO_OK;
 }

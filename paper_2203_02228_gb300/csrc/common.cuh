@@ -67,6 +67,7 @@ struct Colony {
   float rho;
   int32_t min_new_edges;
   int32_t oropt, verify;
+  int32_t ls;            // 1: local search on every new tour; 0: base FACO
   double c_min;          // tau_min / tau_max ratio
   double p_src_gb;
   const int2* xy;        // [n] coordinates, node order

@@ -43,7 +43,7 @@ def test_params_struct_matches_defaults(lib):
     p = params_default()
     assert p.seed == 1 and p.rho == np.float32(0.5) and p.min_new_edges == 8 and p.bl_size == 64
     assert p.p_best == 0.05 and p.p_source_gb == 0.01 and p.oropt == 1 and p.verify_pass == 1
-    assert p.seg_cap == -1
+    assert p.seg_cap == -1 and p.local_search == 1
     assert ctypes.sizeof(faco_params) == 72  # the C layout of include/faco.h on LP64
 
 
@@ -62,7 +62,7 @@ def test_invalid_arguments_are_rejected(lib):
     bad[3, 1] = -1
     assert lib.faco_create(P(bad), 10, 16, ctypes.byref(h)) == _lib.FACO_E_ARG
     for field, val in (("rho", 1.0), ("rho", 0.0), ("p_best", 1.0), ("min_new_edges", 0),
-                       ("bl_size", -1), ("bl_size", 129), ("p_source_gb", 1.5)):
+                       ("bl_size", -1), ("bl_size", 129), ("p_source_gb", 1.5), ("local_search", 2)):
         p = params_default(**{field: val})
         assert lib.faco_create_ex(P(xy), 10, 16, ctypes.byref(p), ctypes.byref(h)) == _lib.FACO_E_ARG
     assert lib.faco_iterate(None, 4, 1) == _lib.FACO_E_ARG

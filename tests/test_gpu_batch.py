@@ -137,3 +137,20 @@ def test_batch512_full_workload_sampled_against_oracle():
         assert lens[i] == oL, i
         np.testing.assert_array_equal(tours[i], ot)
         assert same_bits(b.tau(i), o.tau()), i
+
+
+def test_batch_base_faco():
+    """Base FACO (no local search on new tours) in a batch equals the
+    one-colony path, for both kernel families."""
+    xs = mixed_instances()[:5]
+    for plan in (0, 3):
+        b = Batch(xs, 16, seeds=[21, 22, 23, 24, 25], plan=plan, local_search=0, rho=0.9, min_new_edges=40)
+        b.iterate(10, 5)
+        tours, lens = b.tours()
+        for i, xy in enumerate(xs):
+            c = Colony(xy, 16, seed=21 + i, local_search=0, rho=0.9, min_new_edges=40)
+            c.iterate(10, 5)
+            t, L = c.best()
+            assert lens[i] == L, (plan, i)
+            np.testing.assert_array_equal(tours[i], t)
+            assert same_bits(b.tau(i), c.tau())

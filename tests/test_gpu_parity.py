@@ -126,6 +126,7 @@ CASES = [
     ("tiny9", 9, 4, 30, 16, {}),
     ("tiny4", 4, 3, 10, 16, {}),
     ("tiny3", 3, 2, 5, 16, {}),
+    ("base_faco", 600, 12, 15, 16, dict(local_search=0, rho=0.9, min_new_edges=40)),
 ]
 
 
