@@ -97,8 +97,16 @@ __global__ void __launch_bounds__(32) k_nn_tour_b(const Colony* cols, const Colo
   nn_tour_body(C.xy, C.n, S.cand, C.k, S.backup, C.bl, S.init_route, sv, C.grid, S.cell_start, S.cell_pts);
 }
 
-// Reverse the forward span x..y (or its complement) with the whole block.
-__device__ void cta_flip(ArrTour& T, int x, int y) {
+// Positions reversed by one move (at most three flips): first position and
+// length of each reversed span, appended by thread 0.
+struct SpanLog {
+  int2 span[3];
+  int count;
+};
+
+// Reverse the forward span x..y (or its complement) with the whole block;
+// the span actually reversed goes to the log.
+__device__ void cta_flip(ArrTour& T, int x, int y, SpanLog& log) {
   const int n = T.n;
   __syncthreads();
   int i = T.pos[x], j = T.pos[y];
@@ -113,6 +121,7 @@ __device__ void cta_flip(ArrTour& T, int x, int y) {
     j = j2;
     L = n - L;
   }
+  if (threadIdx.x == 0 && log.count < 3) log.span[log.count++] = make_int2(i, L);
   const int half = L >> 1;
   for (int t = threadIdx.x; t < half; t += blockDim.x) {
     int ia = i + t;
@@ -128,26 +137,45 @@ __device__ void cta_flip(ArrTour& T, int x, int y) {
   __syncthreads();
 }
 
-__device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4) {
+__device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4, SpanLog& log) {
   const bool fwd = T.succ(n1) == n2;
   if (fwd)
-    cta_flip(T, n2, n3);
+    cta_flip(T, n2, n3, log);
   else
-    cta_flip(T, n1, n4);
+    cta_flip(T, n1, n4, log);
 }
 
-// The local search of ls_array.cuh with every node queued (the initial
-// tour), run by one block of 32 warps.  Each round, warp w evaluates the
-// w-th queued node on the current tour; the entries are then popped in
-// queue order up to and including the first one that found a move, which
-// is applied.  Nothing changes the tour between the confirmed evaluations,
-// so the result is exactly that of popping one node at a time.
+// true when position p lies in the cyclic span (first position i, length L).
+__device__ __forceinline__ bool in_span(int p, int2 sp, int n) {
+  int d = p - sp.x;
+  if (d < 0) d += n;
+  return d < sp.y;
+}
+
+// The local search with every node queued (the initial tour), run by one
+// block of 32 warps over a window of the next 32 queued nodes.  Each window
+// entry keeps its evaluation -- the best 2-opt / Or-opt move from its node
+// on the tour as it was -- together with the tour positions that evaluation
+// read (the node's, the next three and the previous one; each candidate's
+// and its two neighbours').  A move reverses spans of positions; an entry
+// whose positions meet none of them would evaluate to the same result, so
+// it is kept, the others are dropped.  Each round pops entries in queue
+// order up to and including the first one whose evaluation found a move,
+// which is applied.  An evaluation runs only when an entry without one
+// comes before the first improving entry (all entries without one are then
+// evaluated, a warp each).  The pops, moves and queue are exactly those of
+// popping one node at a time.
+constexpr int kWin = 32;
+
 __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_t* cand, int k, int oropt,
                                              int verify, int32_t* route, int32_t* pos, int32_t* queue,
                                              uint8_t* flags, int32_t* logb) {
-  __shared__ int64_t s_gain[32];
-  __shared__ int s_mv[32][8];
-  __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win;
+  __shared__ int64_t s_gain[kWin];
+  __shared__ int s_mv[kWin][8];
+  __shared__ int s_node[kWin];            // node whose evaluation the slot holds, -1: none
+  __shared__ int s_dep[kWin][kMaxK + 1];  // [0]: its position, [1 + s]: candidate s's position
+  __shared__ SpanLog s_log;
+  __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win, s_base;
   LsEnv E{n, oropt, verify, queue, flags, logb};
   ArrTour T{n, k, route, pos, xy, cand, k};
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -156,12 +184,13 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
     queue[i] = x;
     flags[x] = 1;
   }
+  if (tid < kWin) s_node[tid] = -1;
   if (tid == 0) {
-    s_qh = 0; s_qn = n; s_nlog = 0; s_changes = 0; s_moves_round = 0;
+    s_qh = 0; s_qn = n; s_nlog = 0; s_changes = 0; s_moves_round = 0; s_base = 0;
   }
   __syncthreads();
   for (;;) {
-    const int qh = s_qh, qn = s_qn;
+    const int qh = s_qh, qn = s_qn, base = s_base;
     if (qn == 0 || s_changes >= n) {
       if (s_changes >= n || !verify || s_moves_round == 0) break;
       const int nl = s_nlog;  // verify round: queue again the nodes popped
@@ -171,57 +200,78 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
         flags[x] = 1;
       }
       __syncthreads();
+      if (tid < kWin) s_node[tid] = -1;  // the queue changed: no evaluation carries over
       if (tid == 0) {
-        s_qh = 0; s_qn = nl; s_nlog = 0; s_moves_round = 0;
+        s_qh = 0; s_qn = nl; s_nlog = 0; s_moves_round = 0; s_base = 0;
       }
       __syncthreads();
       continue;
     }
-    const int W = qn < 32 ? qn : 32;
-    if (w < W) {
-      int idx = qh + w;
+    // window offset `lane` of every warp: its node, slot, and whether its
+    // evaluation is there and improves
+    const int R = qn < kWin ? qn : kWin;
+    const int slot = (base + lane) & (kWin - 1);
+    int node = -1;
+    bool have = false, impr = false;
+    if (lane < R) {
+      int idx = qh + lane;
       if (idx >= n) idx -= n;
-      const int a = queue[idx];
-      int mv2[4], mvo[7];
-      int64_t g2, go;
-      eval_both(T, a, oropt != 0, g2, mv2, go, mvo);
-      if (lane == 0) {
-        if (g2 > 0) {
-          s_gain[w] = g2;
-          for (int t = 0; t < 4; ++t) s_mv[w][t] = mv2[t];
-          s_mv[w][7] = 0;
-        } else {
-          s_gain[w] = go > 0 ? go : 0;
-          for (int t = 0; t < 7; ++t) s_mv[w][t] = mvo[t];
-          s_mv[w][7] = 1;
+      node = queue[idx];
+      have = s_node[slot] == node;
+      impr = have && s_gain[slot] > 0;
+    }
+    const unsigned bimp = __ballot_sync(kFull, impr);
+    const unsigned bmiss = __ballot_sync(kFull, lane < R && !have);
+    const int f = bimp ? __ffs(bimp) - 1 : R;
+    const unsigned before = f >= 32 ? kFull : ((1u << f) - 1u);
+    if (bmiss & before) {  // an entry without an evaluation comes first: evaluate every such entry
+      const int my_node = __shfl_sync(kFull, node, w & 31);
+      const int my_slot = (base + w) & (kWin - 1);
+      if (w < R && ((bmiss >> w) & 1u)) {
+        int mv2[4], mvo[7];
+        int64_t g2, go;
+        eval_both(T, my_node, oropt != 0, g2, mv2, go, mvo);
+        if (lane < k) s_dep[my_slot][1 + lane] = T.pos[T.cand(my_node, lane)];
+        if (lane == 0) {
+          s_dep[my_slot][0] = T.pos[my_node];
+          if (g2 > 0) {
+            s_gain[my_slot] = g2;
+            for (int t = 0; t < 4; ++t) s_mv[my_slot][t] = mv2[t];
+            s_mv[my_slot][7] = 0;
+          } else {
+            s_gain[my_slot] = go > 0 ? go : 0;
+            for (int t = 0; t < 7; ++t) s_mv[my_slot][t] = mvo[t];
+            s_mv[my_slot][7] = 1;
+          }
+          s_node[my_slot] = my_node;
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
     if (w == 0) {
-      const unsigned bal = __ballot_sync(kFull, lane < W && s_gain[lane] > 0);
-      const int first = bal ? __ffs(bal) - 1 : W;
-      const int cnt = bal ? first + 1 : W;  // queue entries popped this round
-      int a = -1;
+      const unsigned bal = __ballot_sync(kFull, lane < R && s_gain[slot] > 0);
+      const int first = bal ? __ffs(bal) - 1 : R;
+      const int cnt = bal ? first + 1 : R;  // queue entries popped this round
       bool first_pop = false;
       if (lane < cnt) {
-        int idx = qh + lane;
-        if (idx >= n) idx -= n;
-        a = queue[idx];
-        const uint8_t f = flags[a];
-        first_pop = !(f & 2);
-        flags[a] = (uint8_t)((f & ~1) | 2);
+        const uint8_t fl = flags[node];
+        first_pop = !(fl & 2);
+        flags[node] = (uint8_t)((fl & ~1) | 2);
       }
       const unsigned fb = __ballot_sync(kFull, first_pop);
-      if (first_pop) logb[s_nlog + __popc(fb & ((1u << lane) - 1u))] = a;
+      if (first_pop) logb[s_nlog + __popc(fb & ((1u << lane) - 1u))] = node;
+      const int win_slot = (base + first) & (kWin - 1);
       __syncwarp();
+      if (lane < cnt && lane != first) s_node[slot] = -1;  // popped: the slots are free
       if (lane == 0) {
         s_nlog += __popc(fb);
         int h = qh + cnt;
         if (h >= n) h -= n;
         s_qh = h;
         s_qn = qn - cnt;
-        s_win = bal ? first : -1;
+        s_base = (base + cnt) & (kWin - 1);
+        s_win = bal ? win_slot : -1;
+        s_log.count = 0;
       }
     }
     __syncthreads();
@@ -229,12 +279,43 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
     if (win >= 0) {
       int mv[8];
       for (int t = 0; t < 8; ++t) mv[t] = s_mv[win][t];
+      __syncthreads();  // every thread has the move before its slot is freed
+      if (tid == 0) s_node[win] = -1;
       if (mv[7] == 0) {
-        cta_flip(T, mv[1], mv[2]);
+        cta_flip(T, mv[1], mv[2], s_log);
       } else {
-        cta_move2(T, mv[0], mv[1], mv[4], mv[5]);
-        cta_move2(T, mv[0], mv[4], mv[3], mv[2]);
-        if (mv[6]) cta_move2(T, mv[4], mv[2], mv[1], mv[5]);
+        cta_move2(T, mv[0], mv[1], mv[4], mv[5], s_log);
+        cta_move2(T, mv[0], mv[4], mv[3], mv[2], s_log);
+        if (mv[6]) cta_move2(T, mv[4], mv[2], mv[1], mv[5], s_log);
+      }
+      // drop the evaluations that read a reversed position (warp w checks slot w)
+      {
+        const int sn = s_node[w];
+        if (sn >= 0) {
+          const int ns = s_log.count;
+          bool hit = false;
+          if (lane < k) {
+            const int tb = s_dep[w][1 + lane];
+            for (int q = 0; q < ns && !hit; ++q) {
+              const int2 sp = s_log.span[q];
+              hit = in_span(tb, sp, n) || in_span(tb == 0 ? n - 1 : tb - 1, sp, n) ||
+                    in_span(tb + 1 == n ? 0 : tb + 1, sp, n);
+            }
+          }
+          if (lane == 31) {
+            const int t0 = s_dep[w][0];
+            for (int q = 0; q < ns && !hit; ++q) {
+              const int2 sp = s_log.span[q];
+              for (int d = -1; d <= 3 && !hit; ++d) {
+                int p = t0 + d;
+                if (p < 0) p += n;
+                if (p >= n) p -= n;
+                hit = in_span(p, sp, n);
+              }
+            }
+          }
+          if (__any_sync(kFull, hit) && lane == 0) s_node[w] = -1;
+        }
       }
       if (w == 0) {
         const int qn2 = ls_push_warp(E, mv, mv[7] == 0 ? 4 : 6, s_qh, s_qn);
