@@ -6,6 +6,12 @@
 
 namespace faco {
 
+int ants_seg_cap_ls(int n, int seg_cap) {
+  if (seg_cap <= 0) return 0;
+  const size_t vis_bytes = ((size_t)((n + 31) >> 5) * 4 + 15) & ~(size_t)15;
+  return segtab_cap_ls(vis_bytes, seg_cap);
+}
+
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs) {
   const size_t vis_bytes = ((size_t)((n + 31) >> 5) * 4 + 15) & ~(size_t)15;
   return segs ? vis_bytes + segtab_bytes(seg_cap) : vis_bytes;

@@ -521,7 +521,7 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
     }
     // hand the tour over: segments in ant order
     const int Sn = *W.tab.S;
-    int4* out = A.segs + (size_t)ant * A.seg_cap;
+    int4* out = A.segs + (size_t)ant * A.seg_cap_ls;
     for (int r = lane; r < Sn; r += 32) {
       const Seg s = W.tab.sg[W.tab.A[r]];
       out[r] = make_int4(s.lo, s.len, s.off, s.rev);

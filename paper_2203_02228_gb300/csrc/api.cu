@@ -363,9 +363,10 @@ int ensure_ants(faco_ctx* c, int m) {
   if (!A.smem_vis) DA(L, A.vis_g, (size_t)m * words);
   // segment-table kernel: one ant per block, bits + table in shared memory
   A.seg_cap = seg_capacity(n, m, c->prm.seg_cap);
+  A.seg_cap_ls = ants_seg_cap_ls(n, A.seg_cap);
   const size_t smem_seg = A.seg_cap > 0 ? ants_smem_per_warp(n, A.seg_cap, true) : 0;
   if (A.seg_cap > 0) {
-    DA(L, A.segs, (size_t)m * A.seg_cap);
+    DA(L, A.segs, (size_t)m * A.seg_cap_ls);
     DA(L, A.nseg, m);
     DA(L, A.redo, m);
     CK(cudaMemsetAsync(A.redo, 0, sizeof(int32_t) * m, c->stream));

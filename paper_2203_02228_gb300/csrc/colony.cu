@@ -169,7 +169,7 @@ __device__ __forceinline__ void best_tour_body(const Colony& C, const Ants& A, i
   } else if (S < 0) {  // source positions
     node = C.src_route[A.route[(size_t)a * n + t]];
   } else {
-    const int4* sg = A.segs + (size_t)a * A.seg_cap;
+    const int4* sg = A.segs + (size_t)a * A.seg_cap_ls;
     int lo = 0, hi = S - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;

@@ -122,7 +122,9 @@ struct Ants {
   int32_t* logb;         // [m][n] nodes popped this round, first pop order
   uint32_t* vis_g;       // [m][words] visited bits when they do not fit shared memory
   int32_t smem_vis;      // 1: visited bits live in shared memory (array kernel)
-  int32_t seg_cap;       // segments per ant table (0: arrays only)
+  int32_t seg_cap;       // segments per ant table during construction (0: arrays only)
+  int32_t seg_cap_ls;    // during the local search, which also takes the visited bits' room;
+                         // the stride of segs
   int4* segs;            // [m][seg_cap] final tours as (lo, len, off, rev), or null
   int32_t* nseg;         // [m] segment count, -1 when the tour is in route/pos
   int32_t* redo;         // [m] 1: the table overflowed, the array kernel redoes the ant

@@ -12,6 +12,8 @@ namespace faco {
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s);
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr);
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs);
+// Segments per ant table during the local search (the visited bits' room added).
+int ants_seg_cap_ls(int n, int seg_cap);
 cudaError_t launch_ants_blk_batch(int kw, const Colony* cols, const Ants* ants, const int2* map, int blocks,
                                   int2* redo_list, int32_t* redo_n, size_t smem, cudaStream_t s);
 // batch array kernel: minb = 2, 4 or 8 blocks per SM (registers per thread

@@ -262,7 +262,8 @@ void antset_layout(AntSet& a, const Group& g, int m, size_t smem_blk, int seg_mo
   for (int i = 0; i < C; ++i) a.hA[i].nseg = B.take<int32_t>(m);
   for (int i = 0; i < C; ++i) {
     a.cap[i] = ant_cap(g.n[i], smem_blk, seg_mode);
-    a.hA[i].segs = B.take<int4>((size_t)m * (a.cap[i] > 0 ? a.cap[i] : 1));
+    a.hA[i].seg_cap_ls = ants_seg_cap_ls(g.n[i], a.cap[i]);
+    a.hA[i].segs = B.take<int4>((size_t)m * (a.cap[i] > 0 ? a.hA[i].seg_cap_ls : 1));
   }
   for (int i = 0; i < C; ++i) {
     Ants& A = a.hA[i];
@@ -313,6 +314,7 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
     Ants A = e.a->hA[e.i];
     if (e.variant != kVarTable || A.seg_cap <= 0) {
       A.seg_cap = 0;
+      A.seg_cap_ls = 0;
       A.segs = nullptr;
       A.nseg = nullptr;
       A.redo = nullptr;

@@ -65,6 +65,65 @@ __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
   return T;
 }
 
+// Table capacity once the visited bits in front of a table of `cap`
+// segments are free (the local search does not need them): the same
+// shared memory, whole multiples of 32 segments added.
+__host__ __device__ constexpr int segtab_cap_ls(size_t vis_bytes, int cap) {
+  return cap + (int)((vis_bytes / (sizeof(Seg) + 5 * sizeof(uint16_t) + 2 * sizeof(int32_t))) & ~(size_t)31);
+}
+
+// Moves the table `from` (placed after the visited bits) to `to` (placed at
+// the start of the same shared memory, larger capacity), with the whole
+// block.  Every array lies lower in `to` than in `from`, by at least the
+// room gained, so copying each array in increasing index order -- all of a
+// chunk's reads before its writes -- never overwrites an entry not yet
+// read.  The scratch array is not copied.
+__device__ __forceinline__ void seg_relayout(const SegTab& from, const SegTab& to) {
+  const int S = *from.S;
+  const int t = threadIdx.x, T = blockDim.x;
+  __syncthreads();
+  for (int c = 0; c < S; c += T) {
+    const int r = c + t;
+    Seg v{0, 0, 0, 0};
+    if (r < S) v = from.sg[r];
+    __syncthreads();
+    if (r < S) to.sg[r] = v;
+    __syncthreads();
+  }
+  for (int c = 0; c < S; c += T) {
+    const int r = c + t;
+    int32_t a = 0, b = 0;
+    if (r < S) {
+      a = from.offA[r];
+      b = from.loB[r];
+    }
+    __syncthreads();
+    if (r < S) {
+      to.offA[r] = a;
+      to.loB[r] = b;
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < S; c += T) {
+    const int r = c + t;
+    uint16_t a = 0, b = 0, k = 0;
+    if (r < S) {
+      a = from.A[r];
+      b = from.B[r];
+      k = from.rankA[r];
+    }
+    __syncthreads();
+    if (r < S) {
+      to.A[r] = a;
+      to.B[r] = b;
+      to.rankA[r] = k;
+    }
+    __syncthreads();
+  }
+  if (t == 0) *to.S = S;
+  __syncthreads();
+}
+
 // Largest r in [0, S) with key[r] <= v (key ascending, key[0] <= v).
 __device__ __forceinline__ int bsearch_le(const int32_t* key, int S, int v) {
   int lo = 0, hi = S - 1;
