@@ -232,6 +232,47 @@ __device__ __forceinline__ void del2(uint16_t* ids, int32_t* keys, uint16_t* ran
   }
 }
 
+// The two inserts of a split in one pass: (idA, keyA) at index rA of
+// A/offA (rankA follows) and (idB, keyB) at index rB of B/loB, both
+// arrays of S entries (warp-collective).
+__device__ __forceinline__ void ins2_both(const SegTab& T, int S, int rA, int idA, int32_t keyA, int rB, int idB,
+                                          int32_t keyB) {
+  const int lane = lane_id();
+  const int lo = rA < rB ? rA : rB;
+  for (int e = S - 1; e >= lo; e -= 32) {
+    const int idx = e - lane;
+    uint16_t va = 0, vb = 0;
+    int32_t ka = 0, kb = 0;
+    if (idx >= rA) {
+      va = T.A[idx];
+      ka = T.offA[idx];
+    }
+    if (idx >= rB) {
+      vb = T.B[idx];
+      kb = T.loB[idx];
+    }
+    __syncwarp();
+    if (idx >= rA) {
+      T.A[idx + 1] = va;
+      T.offA[idx + 1] = ka;
+      T.rankA[va] = (uint16_t)(idx + 1);
+    }
+    if (idx >= rB) {
+      T.B[idx + 1] = vb;
+      T.loB[idx + 1] = kb;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    T.A[rA] = (uint16_t)idA;
+    T.offA[rA] = keyA;
+    T.rankA[idA] = (uint16_t)rA;
+    T.B[rB] = (uint16_t)idB;
+    T.loB[rB] = keyB;
+  }
+  __syncwarp();
+}
+
 // Ensure a segment starts at ant position t (0 < t < n).  Keys are current
 // on entry and on exit.  false: table full.
 static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
@@ -256,11 +297,10 @@ static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
     }
   }
   __syncwarp();
-  ins2(T.A, T.offA, T.rankA, S, r + 1, nid, t);
   if (!s.rev) {
-    ins2(T.B, T.loB, nullptr, S, rb + 1, nid, s.lo + d);
+    ins2_both(T, S, r + 1, nid, t, rb + 1, nid, s.lo + d);
   } else {  // nid keeps the low end: it goes before id, whose lo moved up
-    ins2(T.B, T.loB, nullptr, S, rb, nid, s.lo);
+    ins2_both(T, S, r + 1, nid, t, rb, nid, s.lo);
     if (lane_id() == 0) T.loB[rb + 1] = s.lo + s.len - d;
   }
   if (lane_id() == 0) *T.S = S + 1;
@@ -490,28 +530,35 @@ struct SegTour {
       // R[m] = A[rj - m] (m < clo), A[S - 1 - (m - clo)] (m >= clo)
       for (int m = lane; m < c; m += 32) T.tmp[m] = m < clo ? T.A[rj - m] : T.A[S - 1 - (m - clo)];
       __syncwarp();
-      // new offsets by a sequential prefix over R (lane 0; c is small)
-      int straddle = -1, cut = 0;
-      if (lane == 0) {
-        int pos = i;
-        for (int m = 0; m < c; ++m) {
+      // new offsets: R laid out from position i (a prefix sum of the lengths,
+      // 32 segments at a time), wrapped below n; the segment that crosses
+      // position n (straddle) and how many start below n (nhi)
+      int straddle = -1, cut = 0, nhi = 0, carry = 0;
+      for (int m0 = 0; m0 < c; m0 += 32) {
+        const int m = m0 + lane;
+        int len = 0;
+        if (m < c) len = T.sg[T.tmp[m]].len;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int at = i + carry + incl - len;  // first position of segment m
+        if (m < c) {
           Seg& s = T.sg[T.tmp[m]];
           s.rev ^= 1;
-          s.off = pos;
-          if (pos < n && pos + s.len > n) {
-            straddle = m;
-            cut = n - pos;
-          }
-          pos += s.len;
-          if (pos >= n && s.off >= n) s.off -= n;
+          s.off = at >= n ? at - n : at;
         }
-        for (int m = 0; m < c; ++m) {
-          Seg& s = T.sg[T.tmp[m]];
-          if (s.off >= n) s.off -= n;
+        const unsigned bs = __ballot_sync(kFull, m < c && at < n && at + len > n);
+        if (bs) {
+          const int l = __ffs(bs) - 1;
+          straddle = m0 + l;
+          cut = n - __shfl_sync(kFull, at, l);
         }
+        nhi += __popc(__ballot_sync(kFull, m < c && at < n));
+        carry += __shfl_sync(kFull, incl, 31);
       }
-      straddle = __shfl_sync(kFull, straddle, 0);
-      cut = __shfl_sync(kFull, cut, 0);
       __syncwarp();
       int S2 = S;
       int nid = -1;
@@ -540,18 +587,7 @@ struct SegTour {
       // new A: [nid] + wrapped part of R + middle A[clo..ri) + unwrapped part of R
       // R is ordered by new position: the unwrapped part (offsets >= i) comes
       // first in R, the wrapped part after it.
-      int nhi = 0;  // R entries placed in [i, n): up to and including the straddler
-      if (lane == 0) {
-        int pos = i;
-        nhi = 0;
-        for (int m = 0; m < c; ++m) {
-          if (pos >= n) break;
-          pos += T.sg[T.tmp[m]].len;
-          ++nhi;
-        }
-        if (straddle >= 0) nhi = straddle + 1;
-      }
-      nhi = __shfl_sync(kFull, nhi, 0);
+      // nhi: R entries placed in [i, n), up to and including the straddler
       // assemble into the tail of tmp: tmp[c..c+S2)
       uint16_t* out = T.tmp + c;
       const int mid = ri - clo;
