@@ -152,19 +152,6 @@ __device__ __forceinline__ void u16_insert(uint16_t* arr, int S, int r, uint16_t
   __syncwarp();
 }
 
-// Remove index r of arr[0..S) (warp-collective).
-__device__ __forceinline__ void u16_remove(uint16_t* arr, int S, int r) {
-  const int lane = lane_id();
-  for (int e = r + 1; e < S; e += 32) {
-    const int idx = e + lane;
-    uint16_t v = 0;
-    if (idx < S) v = arr[idx];
-    __syncwarp();
-    if (idx < S) arr[idx - 1] = v;
-    __syncwarp();
-  }
-}
-
 // Rebuild the search keys from the orders (warp-collective).
 __device__ __forceinline__ void segtab_keys(const SegTab& T) {
   const int S = *T.S;
@@ -180,56 +167,6 @@ __device__ __forceinline__ void segtab_keys(const SegTab& T) {
 // Rank in B of segment id (by its lo).
 __device__ __forceinline__ int rank_B(const SegTab& T, int id) {
   return bsearch_le(T.loB, *T.S, T.sg[id].lo);
-}
-
-// Insert (id, key) at index r of the parallel arrays ids/keys[0..S)
-// (warp-collective); rank, when given, follows the moved ids.
-__device__ __forceinline__ void ins2(uint16_t* ids, int32_t* keys, uint16_t* rank, int S, int r, int id,
-                                     int32_t key) {
-  const int lane = lane_id();
-  for (int e = S - 1; e >= r; e -= 32) {
-    const int idx = e - lane;
-    uint16_t v = 0;
-    int32_t k = 0;
-    if (idx >= r) {
-      v = ids[idx];
-      k = keys[idx];
-    }
-    __syncwarp();
-    if (idx >= r) {
-      ids[idx + 1] = v;
-      keys[idx + 1] = k;
-      if (rank) rank[v] = (uint16_t)(idx + 1);
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    ids[r] = (uint16_t)id;
-    keys[r] = key;
-    if (rank) rank[id] = (uint16_t)r;
-  }
-  __syncwarp();
-}
-
-// Remove index r of ids/keys[0..S) (warp-collective).
-__device__ __forceinline__ void del2(uint16_t* ids, int32_t* keys, uint16_t* rank, int S, int r) {
-  const int lane = lane_id();
-  for (int e = r + 1; e < S; e += 32) {
-    const int idx = e + lane;
-    uint16_t v = 0;
-    int32_t k = 0;
-    if (idx < S) {
-      v = ids[idx];
-      k = keys[idx];
-    }
-    __syncwarp();
-    if (idx < S) {
-      ids[idx - 1] = v;
-      keys[idx - 1] = k;
-      if (rank) rank[v] = (uint16_t)(idx - 1);
-    }
-    __syncwarp();
-  }
 }
 
 // The two inserts of a split in one pass: (idA, keyA) at index rA of
@@ -271,6 +208,37 @@ __device__ __forceinline__ void ins2_both(const SegTab& T, int S, int rA, int id
     T.loB[rB] = keyB;
   }
   __syncwarp();
+}
+
+// The two removals of a merge in one pass: index rA of A/offA (rankA
+// follows) and index rB of B/loB, arrays of S entries (warp-collective).
+__device__ __forceinline__ void del_both(const SegTab& T, int S, int rA, int rB) {
+  const int lane = lane_id();
+  for (int e = (rA < rB ? rA : rB) + 1; e < S; e += 32) {
+    const int idx = e + lane;
+    const bool da = idx > rA && idx < S, db = idx > rB && idx < S;
+    uint16_t va = 0, vb = 0;
+    int32_t ka = 0, kb = 0;
+    if (da) {
+      va = T.A[idx];
+      ka = T.offA[idx];
+    }
+    if (db) {
+      vb = T.B[idx];
+      kb = T.loB[idx];
+    }
+    __syncwarp();
+    if (da) {
+      T.A[idx - 1] = va;
+      T.offA[idx - 1] = ka;
+      T.rankA[va] = (uint16_t)(idx - 1);
+    }
+    if (db) {
+      T.B[idx - 1] = vb;
+      T.loB[idx - 1] = kb;
+    }
+    __syncwarp();
+  }
 }
 
 // Ensure a segment starts at ant position t (0 < t < n).  Keys are current
@@ -323,8 +291,7 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
     if (a.rev) T.sg[ia].lo = b.lo;
   }
   __syncwarp();
-  del2(T.A, T.offA, T.rankA, S, r + 1);
-  del2(T.B, T.loB, nullptr, S, rbb);
+  del_both(T, S, r + 1, rbb);
   if (a.rev && lane_id() == 0) T.loB[rbb] = b.lo;  // a slid down to b's rank and took its lo
   __syncwarp();
   // free id ib: move the last id into its slot
@@ -345,30 +312,17 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   __syncwarp();
 }
 
-// Drop id `dead` (already unlinked from A and B): move the last id into
-// its slot.  Orders must be consistent; keys are rebuilt by the caller.
-__device__ __forceinline__ void seg_free_id(const SegTab& T, int dead, int S_after) {
-  const int last = S_after;  // id numbers 0..S_after are in use before the move
-  if (dead == last) return;
-  const int lane = lane_id();
-  // re-point the references to `last`
-  for (int r = lane; r < S_after; r += 32) {
-    if (T.A[r] == last) T.A[r] = (uint16_t)dead;
-    if (T.B[r] == last) T.B[r] = (uint16_t)dead;
-  }
-  __syncwarp();
-  if (lane == 0) T.sg[dead] = T.sg[last];
-  __syncwarp();
-}
-
 // Merge ant-adjacent segments that continue each other in the source
-// (never across ant position 0).  Keys are rebuilt.
+// (never across ant position 0), one pair at a time by seg_merge_at; keys
+// are current on entry and on exit.  A merge at rank r makes no pair
+// before r mergeable, so the scan resumes at r.
 static __device__ __noinline__ void seg_merge_all(const SegTab& T) {
   const int lane = lane_id();
+  int from = 0;
   for (;;) {
     const int S = *T.S;
     int found = -1;
-    for (int r0 = 0; r0 + 1 < S && found < 0; r0 += 32) {
+    for (int r0 = from; r0 + 1 < S && found < 0; r0 += 32) {
       const int r = r0 + lane;
       bool m = false;
       if (r + 1 < S) {
@@ -379,21 +333,8 @@ static __device__ __noinline__ void seg_merge_all(const SegTab& T) {
       if (bal) found = r0 + __ffs(bal) - 1;
     }
     if (found < 0) break;
-    const int ia = T.A[found], ib = T.A[found + 1];
-    const Seg a = T.sg[ia], b = T.sg[ib];
-    const int rbb = rank_B(T, ib);
-    __syncwarp();
-    if (lane == 0) {
-      T.sg[ia].len = a.len + b.len;
-      if (a.rev) T.sg[ia].lo = b.lo;
-    }
-    __syncwarp();
-    u16_remove(T.A, S, found + 1);
-    u16_remove(T.B, S, rbb);
-    seg_free_id(T, ib, S - 1);
-    if (lane == 0) *T.S = S - 1;
-    __syncwarp();
-    segtab_keys(T);
+    seg_merge_at(T, found);
+    from = found;
   }
 }
 
