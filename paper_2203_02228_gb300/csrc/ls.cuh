@@ -413,6 +413,15 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
   }
 }
 
+// Evaluation from a on any tour; representations that can change on the
+// way (a segment table that may move to arrays) provide their own overload
+// that picks one concrete representation per call.
+template <class Tour>
+__device__ __forceinline__ void eval_dispatch(const Tour& T, int a, bool do_or, int64_t& g2, int mv2[4],
+                                              int64_t& go, int mvo[7]) {
+  eval_both(T, a, do_or, g2, mv2, go, mvo);
+}
+
 // Applies an Or-opt move {p,a,e,q,u,v,kept} as edge exchanges.
 template <class Tour>
 __device__ __forceinline__ bool apply_or(Tour& T, const int mv[7], LsStats& S) {
@@ -594,7 +603,7 @@ __device__ __forceinline__ int64_t ls_run_block(const LsEnv& E, Tour& T, const i
       const int a = E.queue[idx];
       int mv2[4], mvo[7];
       int64_t g2, go;
-      eval_both(T, a, E.oropt != 0, g2, mv2, go, mvo);
+      eval_dispatch(T, a, E.oropt != 0, g2, mv2, go, mvo);
       if (lane == 0) {
         if (g2 > 0) {
           sh.gain[w] = g2;

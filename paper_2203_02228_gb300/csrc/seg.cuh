@@ -604,4 +604,15 @@ struct HybTour {
   }
 };
 
+// Evaluation on the representation the hybrid tour holds now (uniform
+// across the block): the table path and the array path stay separate
+// code, instead of a branch in every lookup.
+__device__ __forceinline__ void eval_dispatch(const HybTour& T, int a, bool do_or, int64_t& g2, int mv2[4],
+                                              int64_t& go, int mvo[7]) {
+  if (T.arrays())
+    eval_both(T.ar, a, do_or, g2, mv2, go, mvo);
+  else
+    eval_both(T.sg, a, do_or, g2, mv2, go, mvo);
+}
+
 }  // namespace faco
