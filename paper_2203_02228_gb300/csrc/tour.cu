@@ -224,6 +224,7 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
     const unsigned bmiss = __ballot_sync(kFull, lane < R && !have);
     const int f = bimp ? __ffs(bimp) - 1 : R;
     const unsigned before = f >= 32 ? kFull : ((1u << f) - 1u);
+    __syncthreads();  // every warp has decided (from the same slots) before any slot is written
     if (bmiss & before) {  // an entry without an evaluation comes first: evaluate every such entry
       const int my_node = __shfl_sync(kFull, node, w & 31);
       const int my_slot = (base + w) & (kWin - 1);
