@@ -178,7 +178,11 @@ __device__ __forceinline__ uint64_t sqdist(int2 a, int2 b) {
 }
 
 __device__ __forceinline__ int32_t euc2d_m(uint64_t m) {
-  uint32_t r = (uint32_t)__fsqrt_rn(__ull2float_rn(m));  // within 2 of floor(sqrt(m))
+  // a first guess from the hardware reciprocal square root (close for the
+  // short edges that dominate; any guess works), then exact integer steps
+  // to floor(sqrt(m))
+  const float x = __ull2float_rn(m);
+  uint32_t r = m ? (uint32_t)(x * rsqrtf(x)) : 0u;
   uint64_t rr = (uint64_t)r * r;
   while (rr > m) {
     --r;
@@ -262,6 +266,18 @@ __device__ __forceinline__ void warp_min_key(uint64_t& key, int32_t& idx) {
 }
 
 // Maximum gain, ties to the smallest order index; every lane gets it.
+__device__ __forceinline__ void warp_max_gain(int32_t& g, int32_t& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int32_t g2 = __shfl_xor_sync(kFull, g, o);
+    const int32_t i2 = __shfl_xor_sync(kFull, idx, o);
+    if (g2 > g || (g2 == g && i2 < idx)) {
+      g = g2;
+      idx = i2;
+    }
+  }
+}
+
 __device__ __forceinline__ void warp_max_gain(int64_t& g, int32_t& idx) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

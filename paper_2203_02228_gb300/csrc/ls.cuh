@@ -295,23 +295,25 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
     T.nbrs(a, p, s1);
   const int2 xa = T.coord(a), x1 = T.coord(s1), xp = T.coord(p);
   const int d_as = euc2d(xa, x1), d_ap = euc2d(xp, xa);
-  int64_t rem1 = 0, rem2 = 0, rem3 = 0;
+  // gains in 32 bits: each is a signed sum of at most six EUC_2D costs of
+  // coordinates below 2^24 (each cost below 2^25)
+  int32_t rem1 = 0, rem2 = 0, rem3 = 0;
   int2 x2 = xa, x3 = xa;
   if (do_or) {
     x2 = T.coord(s2);
     x3 = T.coord(s3);
-    rem1 = (int64_t)d_ap + d_as - euc2d(xp, x1);
-    rem2 = (int64_t)d_ap + euc2d(x1, x2) - euc2d(xp, x2);
-    rem3 = (int64_t)d_ap + euc2d(x2, x3) - euc2d(xp, x3);
+    rem1 = d_ap + d_as - euc2d(xp, x1);
+    rem2 = d_ap + euc2d(x1, x2) - euc2d(xp, x2);
+    rem3 = d_ap + euc2d(x2, x3) - euc2d(xp, x3);
   }
-  int64_t b2 = 0, bo = 0;
+  int32_t b2 = 0, bo = 0;
   int i2 = INT_MAX, io = INT_MAX;
   const int passes = k <= 16 ? 1 : 2;
   for (int pass = 0; pass < passes; ++pass) {
     const int side = k <= 16 ? (lane >> 4) : pass;
     const int s = k <= 16 ? (lane & 15) : lane;
-    int64_t g = 0;
-    int64_t lo = 0;
+    int32_t g = 0;
+    int32_t lo = 0;
     int li = INT_MAX;
     if (s < k) {
       const int b = T.cand(a, s);
@@ -320,9 +322,9 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
       const int d_ab = euc2d(xa, xb);
       const int d_bbn = euc2d(xb, xbn);
       if (side == 0) {
-        if (d_as > d_ab) g = (int64_t)d_as + d_bbn - d_ab - euc2d(x1, xbn);
+        if (d_as > d_ab) g = d_as + d_bbn - d_ab - euc2d(x1, xbn);
       } else {
-        if (d_ap > d_ab) g = (int64_t)d_ap + d_bbn - d_ab - euc2d(xp, xbn);
+        if (d_ap > d_ab) g = d_ap + d_bbn - d_ab - euc2d(xp, xbn);
       }
       if (do_or) {
         // the tour edge (u, v) at b: (b, succ b) or (pred b, b)
@@ -339,9 +341,9 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
           if (l >= 2) bad |= (u == s1 || v == s1);
           if (l >= 3) bad |= (u == s2 || v == s2);
           if (bad) continue;
-          const int64_t rem = l == 1 ? rem1 : (l == 2 ? rem2 : rem3);
+          const int32_t rem = l == 1 ? rem1 : (l == 2 ? rem2 : rem3);
           if (l == 1) {  // one node: only the reversed form, u-a-v
-            const int64_t gg = rem + d_uv - d_ua - d_av;
+            const int32_t gg = rem + d_uv - d_ua - d_av;
             if (gg > lo) {
               lo = gg;
               li = (s * 2 + side) * 2;
@@ -350,12 +352,12 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
             const int2 xe = l == 2 ? x1 : x2;
             const int d_ue = euc2d(xu, xe), d_ev = euc2d(xe, xv);
             const int base = (((l - 1) * k + s) * 2 + side) * 2;
-            const int64_t g0 = rem + d_uv - d_ue - d_av;  // reversed: u-e ... a-v
+            const int32_t g0 = rem + d_uv - d_ue - d_av;  // reversed: u-e ... a-v
             if (g0 > lo) {
               lo = g0;
               li = base;
             }
-            const int64_t g1 = rem + d_uv - d_ua - d_ev;  // kept: u-a ... e-v
+            const int32_t g1 = rem + d_uv - d_ua - d_ev;  // kept: u-a ... e-v
             if (g1 > lo) {
               lo = g1;
               li = base + 1;
