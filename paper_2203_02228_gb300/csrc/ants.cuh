@@ -513,7 +513,7 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
   LsStats S{0, 0, 0, 0, 0};
   int64_t gain;
   if (SEGS) {
-    SegTour T{n, C.k, C.kw, W.tab, C.XYsrc, C.Csrc};
+    SegTour T{n, C.k, C.kw, W.tab, C.XYsrc, C.Csrc, C.Dcsrc};
     gain = C.ls ? ls_run(E, T, chk, W.nchk, S) : 0;
     if (gain < 0) {  // the table filled up during the search
       if (lane == 0) A.redo[ant] = 1;
@@ -529,7 +529,7 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
     if (lane == 0) A.nseg[ant] = Sn;
     if (A.keep_tours) seg_materialize(C, W.tab, route);
   } else {
-    ArrTour T{n, C.k, route, pos, C.xy, C.cand, C.k};
+    ArrTour T{n, C.k, route, pos, C.xy, C.cand, C.k, C.dcand};
     gain = C.ls ? ls_run(E, T, chk, W.nchk, S) : 0;
     if (lane == 0 && A.nseg) A.nseg[ant] = -1;  // tour is in route/pos
   }

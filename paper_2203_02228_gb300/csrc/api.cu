@@ -28,6 +28,8 @@ struct faco_ctx {
   int32_t *src_route = nullptr, *src_pos = nullptr, *gb_route = nullptr, *gb_pos = nullptr;
   float* Wsrc = nullptr;
   int32_t* Csrc = nullptr;
+  int32_t* Dcsrc = nullptr;
+  int32_t* dcand = nullptr;
   int2* XYsrc = nullptr;
   int32_t* Dsrc = nullptr;
   int64_t* Psrc = nullptr;
@@ -104,6 +106,7 @@ Colony colony_view(const faco_ctx* c) {
   C.xy = c->xy; C.cand = c->cand; C.backup = c->backup; C.eta = c->eta; C.tau = c->tau;
   C.src_route = c->src_route; C.src_pos = c->src_pos; C.gb_route = c->gb_route; C.gb_pos = c->gb_pos;
   C.Wsrc = c->Wsrc; C.Csrc = c->Csrc; C.XYsrc = c->XYsrc; C.Dsrc = c->Dsrc; C.Psrc = c->Psrc;
+  C.Dcsrc = c->Dcsrc; C.dcand = c->dcand;
   C.st = c->st;
   C.grid = c->grid;
   C.cell_start = c->cell_start;
@@ -210,6 +213,8 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     DA(L, c->gb_pos, n);
     DA(L, c->Wsrc, (size_t)n * c->kw);
     DA(L, c->Csrc, (size_t)n * c->kw);
+    DA(L, c->Dcsrc, (size_t)n * c->kw);
+    DA(L, c->dcand, (size_t)n * c->k);
     DA(L, c->XYsrc, n);
     DA(L, c->Dsrc, n);
     DA(L, c->Psrc, (size_t)n + 1);
@@ -261,7 +266,7 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     }
     c->grid = g;
     int32_t *cs = c->cell_start, *cp = c->cell_pts;
-    if (build_lists(c->xy, n, c->k, c->bl, g, cc, cs, cp, c->cand, c->backup, c->eta, s) != cudaSuccess) {
+    if (build_lists(c->xy, n, c->k, c->bl, g, cc, cs, cp, c->cand, c->backup, c->eta, c->dcand, s) != cudaSuccess) {
       free_tmp();
       return FACO_E_CUDA;
     }
@@ -284,7 +289,7 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     if (e == cudaSuccess) e = launch_positions(c->init_route, c->src_pos, n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fl, 0, n, s);
     if (e == cudaSuccess)
-      e = launch_init_ls(c->xy, n, c->cand, c->k, prm.oropt, prm.verify_pass, c->init_route,
+      e = launch_init_ls(c->xy, n, c->cand, c->dcand, c->k, prm.oropt, prm.verify_pass, c->init_route,
                          c->src_pos, q, fl, lg, s);
     if (e == cudaSuccess) e = launch_tour_length(c->xy, c->init_route, n, c->len_tmp, s);
     Colony C = colony_view(c);

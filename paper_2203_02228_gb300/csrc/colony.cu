@@ -38,10 +38,12 @@ __device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
     C.tau[idx] = t;
     C.Wsrc[(size_t)p * kw + s] = __fmul_rn(t, C.eta[idx]);
     C.Csrc[(size_t)p * kw + s] = C.src_pos[v];
+    C.Dcsrc[(size_t)p * kw + s] = C.dcand[idx];
   }
   for (int s = k; s < kw; ++s) {
     C.Wsrc[(size_t)p * kw + s] = 0.0f;
     C.Csrc[(size_t)p * kw + s] = -1;
+    C.Dcsrc[(size_t)p * kw + s] = 0;
   }
   const int2 xu = C.xy[u];
   C.XYsrc[p] = xu;

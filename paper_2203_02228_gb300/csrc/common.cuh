@@ -74,6 +74,7 @@ struct Colony {
   const int32_t* cand;   // [n][k] candidate lists
   const int32_t* backup; // [n][bl] backup lists
   const float* eta;      // [n][k] 1/d
+  const int32_t* dcand;  // [n][k] d, the EUC_2D cost of each candidate edge
   float* tau;            // [n][k] pheromone on candidate edges
   int32_t* src_route;    // [n] source solution
   int32_t* src_pos;      // [n] its inverse
@@ -81,6 +82,7 @@ struct Colony {
   int32_t* gb_pos;       // [n]
   float* Wsrc;           // [n][kw] tau*eta in source order, 0 beyond k
   int32_t* Csrc;         // [n][kw] source position of each candidate, -1 beyond k
+  int32_t* Dcsrc;        // [n][kw] cost of each candidate edge in source order, 0 beyond k
   int2* XYsrc;           // [n] coordinates in source order
   int32_t* Dsrc;         // [n] length of source edge (p, p+1)
   int64_t* Psrc;         // [n+1] exclusive prefix sums of Dsrc
@@ -101,6 +103,7 @@ struct ColonySetup {
   int32_t* cand;         // [n][k]
   int32_t* backup;       // [n][bl]
   float* eta;            // [n][k]
+  int32_t* dcand;        // [n][k]
   int32_t* init_route;   // [n] nearest-neighbour tour, then locally optimal
   int32_t* queue;        // [n] local search of the initial tour
   uint8_t* flags;        // [n]

@@ -105,7 +105,7 @@ __global__ void k_cell_fill(const int2* xy, int n, Grid g, int32_t* cursor, int3
 
 __device__ __forceinline__ void knn_body(const int2* xy, int n, const Grid& g, const int32_t* start,
                                          const int32_t* pts, int k, int bl, int32_t* cand, int32_t* backup,
-                                         float* eta, int u) {
+                                         float* eta, int32_t* dcand, int u) {
   if (u >= n) return;
   const int K = k + bl;
   uint64_t bm[kMaxKnn];
@@ -160,14 +160,15 @@ __device__ __forceinline__ void knn_body(const int2* xy, int n, const Grid& g, c
     cand[(size_t)u * k + s] = bi[s];
     const int32_t d = euc2d_m(bm[s]);
     eta[(size_t)u * k + s] = d > 0 ? __fdiv_rn(1.0f, (float)d) : 1.0f;
+    if (dcand) dcand[(size_t)u * k + s] = d;
   }
   for (int j = 0; j < bl; ++j) backup[(size_t)u * bl + j] = bi[k + j];
 }
 
 __global__ void __launch_bounds__(128) k_knn(const int2* xy, int n, Grid g, const int32_t* start,
                                              const int32_t* pts, int k, int bl, int32_t* cand,
-                                             int32_t* backup, float* eta) {
-  knn_body(xy, n, g, start, pts, k, bl, cand, backup, eta, blockIdx.x * blockDim.x + threadIdx.x);
+                                             int32_t* backup, float* eta, int32_t* dcand) {
+  knn_body(xy, n, g, start, pts, k, bl, cand, backup, eta, dcand, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(128) k_knn_b(const Colony* cols, const ColonyS
   const int2 e = map[blockIdx.x];
   const Colony C = cols[e.x];
   const ColonySetup S = sets[e.x];
-  knn_body(C.xy, C.n, C.grid, S.cell_start, S.cell_pts, C.k, C.bl, S.cand, S.backup, S.eta,
+  knn_body(C.xy, C.n, C.grid, S.cell_start, S.cell_pts, C.k, C.bl, S.cand, S.backup, S.eta, S.dcand,
            e.y * blockDim.x + threadIdx.x);
 }
 
@@ -270,7 +271,7 @@ cudaError_t launch_bbox_check(const int2* xy, int n, int32_t* out5, cudaStream_t
 
 cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int32_t* cell_count,
                         int32_t* cell_start, int32_t* cell_pts, int32_t* cand, int32_t* backup,
-                        float* eta, cudaStream_t s) {
+                        float* eta, int32_t* dcand, cudaStream_t s) {
   const int cells = g.gx * g.gy;
   cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * cells, s);
   if (e != cudaSuccess) return e;
@@ -279,7 +280,7 @@ cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int
   e = cudaMemcpyAsync(cell_count, cell_start, sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(xy, n, g, cell_count, cell_pts);
-  k_knn<<<(n + 127) / 128, 128, 0, s>>>(xy, n, g, cell_start, cell_pts, k, bl, cand, backup, eta);
+  k_knn<<<(n + 127) / 128, 128, 0, s>>>(xy, n, g, cell_start, cell_pts, k, bl, cand, backup, eta, dcand);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct ArrTour {
   const int2* xy;       // coordinates by node
   const int32_t* cn;    // candidate lists by node [n][stride]
   int stride;
+  const int32_t* cd;    // their EUC_2D costs, same layout
   __device__ __forceinline__ int pos_of(int x) const { return pos[x]; }
   __device__ __forceinline__ int at_off(int p, int d) const {
     p += d;
@@ -81,6 +82,7 @@ struct ArrTour {
   }
   __device__ __forceinline__ int2 coord(int x) const { return xy[x]; }
   __device__ __forceinline__ int cand(int x, int s) const { return cn[(size_t)x * stride + s]; }
+  __device__ __forceinline__ int cdist(int x, int s) const { return cd[(size_t)x * stride + s]; }
 
   // Reverse the forward span x..y (or its complement when longer than n/2).
   __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {
@@ -139,148 +141,8 @@ __device__ __forceinline__ bool tour_move2(Tour& T, int n1, int n2, int n3, int 
   return T.flip(n1, n4, S);
 }
 
-// Best improving 2-opt move from a; returns the gain (0: none) and the move
-// (w,x,y,z) with w->x and y->z removed, flip x..y.
-template <class Tour>
-__device__ __forceinline__ int64_t eval_2opt(const Tour& T, int a, int mv[4]) {
-  const int k = T.k, lane = lane_id();
-  int a_pred, a_succ;
-  T.nbrs(a, a_pred, a_succ);
-  const int2 xa = T.coord(a), xs = T.coord(a_succ), xp = T.coord(a_pred);
-  const int d_as = euc2d(xa, xs), d_ap = euc2d(xp, xa);
-  int64_t best = 0;
-  int bidx = INT_MAX;
-  const int passes = k <= 16 ? 1 : 2;
-  for (int pass = 0; pass < passes; ++pass) {
-    const int side = k <= 16 ? (lane >> 4) : pass;
-    const int s = k <= 16 ? (lane & 15) : lane;
-    int64_t g = 0;
-    if (s < k) {
-      const int b = T.cand(a, s);
-      const int bn = side == 0 ? T.succ(b) : T.pred(b);
-      const int2 xb = T.coord(b), xbn = T.coord(bn);
-      const int d_ab = euc2d(xa, xb);
-      if (side == 0) {
-        if (d_as > d_ab) g = (int64_t)d_as + euc2d(xb, xbn) - d_ab - euc2d(xs, xbn);
-      } else {
-        if (d_ap > d_ab) g = (int64_t)d_ap + euc2d(xbn, xb) - d_ab - euc2d(xp, xbn);
-      }
-    }
-    int idx = side * k + s;
-    if (!(g > 0)) {
-      g = 0;
-      idx = INT_MAX;
-    }
-    warp_max_gain(g, idx);
-    if (g > best) {
-      best = g;
-      bidx = idx;
-    }
-  }
-  if (best > 0) {
-    const int side = bidx / k, s = bidx % k;
-    const int b = T.cand(a, s);
-    if (side == 0) {
-      mv[0] = a; mv[1] = a_succ; mv[2] = b; mv[3] = T.succ(b);
-    } else {
-      mv[0] = a_pred; mv[1] = a; mv[2] = T.pred(b); mv[3] = b;
-    }
-  }
-  return best;
-}
-
-// Best improving Or-opt move from a (definition in the file comment).
-// mv = {p, a, e, q, u, v, kept}.
-template <class Tour>
-__device__ __forceinline__ int64_t eval_or(const Tour& T, int a, int mv[7]) {
-  const int n = T.n, k = T.k, lane = lane_id();
-  if (n < 8) return 0;
-  int p, s1, s2, s3;
-  T.walk(a, p, s1, s2, s3);
-  const int2 xa = T.coord(a), xp = T.coord(p), x1 = T.coord(s1), x2 = T.coord(s2), x3 = T.coord(s3);
-  const int d_pa = euc2d(xp, xa);
-  // l = 1: e = a, q = s1;  l = 2: e = s1, q = s2;  l = 3: e = s2, q = s3
-  const int64_t rem1 = (int64_t)d_pa + euc2d(xa, x1) - euc2d(xp, x1);
-  const int64_t rem2 = (int64_t)d_pa + euc2d(x1, x2) - euc2d(xp, x2);
-  const int64_t rem3 = (int64_t)d_pa + euc2d(x2, x3) - euc2d(xp, x3);
-  int64_t lbest = 0;
-  int lidx = INT_MAX;
-  const int passes = k <= 16 ? 1 : 2;
-  for (int pass = 0; pass < passes; ++pass) {
-    const int side = k <= 16 ? (lane >> 4) : pass;
-    const int s = k <= 16 ? (lane & 15) : lane;
-    if (s < k) {
-      const int b = T.cand(a, s);
-      int u, v;
-      if (side == 0) {
-        u = b;
-        v = T.succ(b);
-      } else {
-        u = T.pred(b);
-        v = b;
-      }
-      const int2 xu = T.coord(u), xv = T.coord(v);
-      const int d_uv = euc2d(xu, xv);
-      const int d_ua = euc2d(xu, xa), d_av = euc2d(xa, xv);
-      const bool base_bad = (u == p || v == p || u == a || v == a);
-#pragma unroll
-      for (int l = 1; l <= 3; ++l) {
-        const int q = l == 1 ? s1 : (l == 2 ? s2 : s3);
-        bool bad = base_bad || u == q || v == q;
-        if (l >= 2) bad |= (u == s1 || v == s1);
-        if (l >= 3) bad |= (u == s2 || v == s2);
-        if (bad) continue;
-        const int64_t rem = l == 1 ? rem1 : (l == 2 ? rem2 : rem3);
-        if (l == 1) {  // one node: only the reversed form, u-a-v
-          const int64_t g = rem + d_uv - d_ua - d_av;
-          if (g > lbest) {
-            lbest = g;
-            lidx = ((s * 2 + side) * 2);
-          }
-        } else {
-          const int2 xe = l == 2 ? x1 : x2;
-          const int d_ue = euc2d(xu, xe), d_ev = euc2d(xe, xv);
-          const int base = (((l - 1) * k + s) * 2 + side) * 2;
-          const int64_t g0 = rem + d_uv - d_ue - d_av;  // reversed: u-e ... a-v
-          if (g0 > lbest) {
-            lbest = g0;
-            lidx = base;
-          }
-          const int64_t g1 = rem + d_uv - d_ua - d_ev;  // kept: u-a ... e-v
-          if (g1 > lbest) {
-            lbest = g1;
-            lidx = base + 1;
-          }
-        }
-      }
-    }
-  }
-  if (!(lbest > 0)) {
-    lbest = 0;
-    lidx = INT_MAX;
-  }
-  warp_max_gain(lbest, lidx);
-  if (lbest > 0) {
-    const int kept = lidx & 1, side = (lidx >> 1) & 1, rest = lidx >> 2;
-    const int s = rest % k, l = rest / k + 1;
-    const int b = T.cand(a, s);
-    int u, v;
-    if (side == 0) {
-      u = b;
-      v = T.succ(b);
-    } else {
-      u = T.pred(b);
-      v = b;
-    }
-    mv[0] = p; mv[1] = a; mv[2] = l == 1 ? a : (l == 2 ? s1 : s2);
-    mv[3] = l == 1 ? s1 : (l == 2 ? s2 : s3); mv[4] = u; mv[5] = v; mv[6] = kept;
-  }
-  return lbest;
-}
-
 // Both scans from a in one pass over NN(a) (one lookup of a, one of each
-// neighbour b): the best 2-opt move (as eval_2opt) and, when do_or, the best
-// Or-opt move (as eval_or).  The search then takes the 2-opt move if it
+// neighbour b): the best 2-opt move and, when do_or, the best Or-opt move.  The search then takes the 2-opt move if it
 // gains, else the Or-opt move -- the same decision as scanning one after the
 // other.
 template <class Tour>
@@ -319,7 +181,7 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
       const int b = T.cand(a, s);
       const int bn = side == 0 ? T.succ(b) : T.pred(b);
       const int2 xb = T.coord(b), xbn = T.coord(bn);
-      const int d_ab = euc2d(xa, xb);
+      const int d_ab = T.cdist(a, s);  // = euc2d(xa, xb), kept with the lists
       const int d_bbn = euc2d(xb, xbn);
       if (side == 0) {
         if (d_as > d_ab) g = d_as + d_bbn - d_ab - euc2d(x1, xbn);

@@ -163,6 +163,10 @@ void group_layout(Group& g, char* base) {
     g.hS[i].eta = B.take<float>((size_t)g.n[i] * g.k[i]);
     g.hC[i].eta = g.hS[i].eta;
   }
+  for (int i = 0; i < C; ++i) {
+    g.hS[i].dcand = B.take<int32_t>((size_t)g.n[i] * g.k[i]);
+    g.hC[i].dcand = g.hS[i].dcand;
+  }
   for (int i = 0; i < C; ++i) g.hC[i].tau = B.take<float>((size_t)g.n[i] * g.k[i]);
   for (int i = 0; i < C; ++i) g.hC[i].src_route = B.take<int32_t>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hC[i].src_pos = B.take<int32_t>(g.n[i]);
@@ -170,6 +174,7 @@ void group_layout(Group& g, char* base) {
   for (int i = 0; i < C; ++i) g.hC[i].gb_pos = B.take<int32_t>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hC[i].Wsrc = B.take<float>((size_t)g.n[i] * g.kw);
   for (int i = 0; i < C; ++i) g.hC[i].Csrc = B.take<int32_t>((size_t)g.n[i] * g.kw);
+  for (int i = 0; i < C; ++i) g.hC[i].Dcsrc = B.take<int32_t>((size_t)g.n[i] * g.kw);
   for (int i = 0; i < C; ++i) g.hC[i].XYsrc = B.take<int2>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hC[i].Dsrc = B.take<int32_t>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hC[i].Psrc = B.take<int64_t>((size_t)g.n[i] + 1);

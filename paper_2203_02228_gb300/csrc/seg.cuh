@@ -344,6 +344,7 @@ struct SegTour {
   SegTab T;
   const int2* xy;       // coordinates by source position
   const int32_t* cn;    // candidate source positions by source position [n][kw]
+  const int32_t* cd;    // their EUC_2D costs, same layout
 
   // Lookups stay in [0, n) even if the table were inconsistent (which would
   // be a library bug: it is flagged and shows up as a wrong tour, not as an
@@ -363,6 +364,7 @@ struct SegTour {
   }
   __device__ __forceinline__ int2 coord(int q) const { return xy[q]; }
   __device__ __forceinline__ int cand(int q, int s) const { return cn[(size_t)q * kw + s]; }
+  __device__ __forceinline__ int cdist(int q, int s) const { return cd[(size_t)q * kw + s]; }
 
   // Segment id holding source position q.
   __device__ __forceinline__ int locate(int q) const { return T.B[bsearch_le(T.loB, *T.S, q)]; }
@@ -578,6 +580,7 @@ struct HybTour {
   }
   __device__ __forceinline__ int2 coord(int x) const { return sg.coord(x); }
   __device__ __forceinline__ int cand(int x, int s) const { return sg.cand(x, s); }
+  __device__ __forceinline__ int cdist(int x, int s) const { return sg.cdist(x, s); }
 
   __device__ __noinline__ void to_arrays() {
     const int S = *sg.T.S;

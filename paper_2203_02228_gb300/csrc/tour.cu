@@ -167,9 +167,9 @@ __device__ __forceinline__ bool in_span(int p, int2 sp, int n) {
 // popping one node at a time.
 constexpr int kWin = 32;
 
-__device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_t* cand, int k, int oropt,
-                                             int verify, int32_t* route, int32_t* pos, int32_t* queue,
-                                             uint8_t* flags, int32_t* logb) {
+__device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_t* cand, const int32_t* dcand,
+                                             int k, int oropt, int verify, int32_t* route, int32_t* pos,
+                                             int32_t* queue, uint8_t* flags, int32_t* logb) {
   __shared__ int64_t s_gain[kWin];
   __shared__ int s_mv[kWin][8];
   __shared__ int s_node[kWin];            // node whose evaluation the slot holds, -1: none
@@ -177,7 +177,7 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
   __shared__ SpanLog s_log;
   __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win, s_base;
   LsEnv E{n, oropt, verify, queue, flags, logb};
-  ArrTour T{n, k, route, pos, xy, cand, k};
+  ArrTour T{n, k, route, pos, xy, cand, k, dcand};
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   for (int i = tid; i < n; i += blockDim.x) {
     const int x = route[i];
@@ -339,17 +339,19 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
   for (int i = tid; i < nl; i += blockDim.x) flags[logb[i]] = 0;
 }
 
-__global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand, int k,
-                                                  int oropt, int verify, int32_t* route, int32_t* pos,
-                                                  int32_t* queue, uint8_t* flags, int32_t* logb) {
-  init_ls_body(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
+__global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand,
+                                                  const int32_t* dcand, int k, int oropt, int verify,
+                                                  int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
+                                                  int32_t* logb) {
+  init_ls_body(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
 }
 
 // Batch: one block per colony; positions of the initial tour in src_pos.
 __global__ void __launch_bounds__(1024) k_init_ls_b(const Colony* cols, const ColonySetup* sets) {
   const Colony C = cols[blockIdx.x];
   const ColonySetup S = sets[blockIdx.x];
-  init_ls_body(C.xy, C.n, S.cand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags, S.logb);
+  init_ls_body(C.xy, C.n, S.cand, S.dcand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags,
+               S.logb);
 }
 
 // what = 0: Philox draws   in: uint32 [count][4] = (idx, ant, iter, tag) -> out uint32
@@ -394,10 +396,10 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, int k, int oropt, int verify,
-                           int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
+cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
+                           int verify, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s) {
-  k_init_ls<<<1, 1024, 0, s>>>(xy, n, cand, k, oropt, verify, route, pos, queue, flags, logb);
+  k_init_ls<<<1, 1024, 0, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
   return cudaGetLastError();
 }
 
