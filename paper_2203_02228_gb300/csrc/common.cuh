@@ -255,30 +255,26 @@ __device__ __forceinline__ int64_t shfl64_up(int64_t v, int o) {
   return (int64_t)__shfl_up_sync(kFull, (unsigned long long)v, o);
 }
 
-// Lexicographic minimum of (key, idx) over the warp; every lane gets it.
+// Lexicographic minimum of (key, idx) over the warp, for idx >= 0; every
+// lane gets it.  Three warp reductions: the key's high word, its low word
+// among the lanes with that high word, the index among the lanes with that
+// key.
 __device__ __forceinline__ void warp_min_key(uint64_t& key, int32_t& idx) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t k2 = __shfl_xor_sync(kFull, (unsigned long long)key, o);
-    const int32_t i2 = __shfl_xor_sync(kFull, idx, o);
-    if (k2 < key || (k2 == key && i2 < idx)) {
-      key = k2;
-      idx = i2;
-    }
-  }
+  const unsigned kh = (unsigned)(key >> 32);
+  const unsigned hi = __reduce_min_sync(kFull, kh);
+  const unsigned lo = __reduce_min_sync(kFull, kh == hi ? (unsigned)key : 0xFFFFFFFFu);
+  const uint64_t km = ((uint64_t)hi << 32) | lo;
+  idx = (int32_t)__reduce_min_sync(kFull, key == km ? (unsigned)idx : 0xFFFFFFFFu);
+  key = km;
 }
 
 // Maximum gain, ties to the smallest order index; every lane gets it.
+// For gains >= 0 and indices >= 0: two warp reductions (the largest gain,
+// then the smallest index among the lanes holding it).
 __device__ __forceinline__ void warp_max_gain(int32_t& g, int32_t& idx) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const int32_t g2 = __shfl_xor_sync(kFull, g, o);
-    const int32_t i2 = __shfl_xor_sync(kFull, idx, o);
-    if (g2 > g || (g2 == g && i2 < idx)) {
-      g = g2;
-      idx = i2;
-    }
-  }
+  const int32_t gm = __reduce_max_sync(kFull, g);
+  idx = (int32_t)__reduce_min_sync(kFull, g == gm ? (unsigned)idx : 0xFFFFFFFFu);
+  g = gm;
 }
 
 __device__ __forceinline__ void warp_max_gain(int64_t& g, int32_t& idx) {

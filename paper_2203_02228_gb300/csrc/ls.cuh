@@ -24,10 +24,11 @@
 //              {pred a, succ e}; applied as two or three edge exchanges.
 //
 // A Tour provides (device, lane-local unless noted): n, k; pos_of(x);
-// succ(x), pred(x); nbrs(x, pred, succ); walk(a, pred, s1, s2, s3) (the
-// predecessor and three successors); coord(x); cand(x, s); and the
-// warp-collective flip(x, y, S) (false when the representation ran out of
-// capacity).
+// succ(x), pred(x); adj(x, up) (succ when up, else pred, one code path for
+// lanes that differ in direction); nbrs(x, pred, succ); walk(a, pred, s1,
+// s2, s3) (the predecessor and three successors); coord(x); cand(x, s);
+// cdist(x, s) (the cost of that candidate edge); and the warp-collective
+// flip(x, y, S) (false when the representation ran out of capacity).
 #pragma once
 
 #include <climits>
@@ -68,6 +69,7 @@ struct ArrTour {
   }
   __device__ __forceinline__ int succ(int x) const { return at_off(pos[x], 1); }
   __device__ __forceinline__ int pred(int x) const { return at_off(pos[x], -1); }
+  __device__ __forceinline__ int adj(int x, bool up) const { return at_off(pos[x], up ? 1 : -1); }
   __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
     const int t = pos[x];
     p = at_off(t, -1);
@@ -142,46 +144,66 @@ __device__ __forceinline__ bool tour_move2(Tour& T, int n1, int n2, int n3, int 
 }
 
 // Both scans from a in one pass over NN(a) (one lookup of a, one of each
-// neighbour b): the best 2-opt move and, when do_or, the best Or-opt move.  The search then takes the 2-opt move if it
-// gains, else the Or-opt move -- the same decision as scanning one after the
-// other.
+// neighbour b): the best 2-opt move and, when do_or, the best Or-opt move.
+// The search then takes the 2-opt move if it gains, else the Or-opt move --
+// the same decision as scanning one after the other.  Lane layout: with
+// k <= 16, lane = side * 16 + s (side 0: the edge (b, succ b), side 1:
+// (pred b, b)); with k > 16, lane = s and the two sides are two passes.
+// The loads that do not depend on the walk from a (the candidate row, b's
+// coordinates) are issued before it; the move is rebuilt from the winning
+// lane's registers.
 template <class Tour>
 __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int64_t& g2, int mv2[4],
                                           int64_t& go, int mvo[7]) {
   const int n = T.n, k = T.k, lane = lane_id();
   do_or = do_or && n >= 8;
+  const bool two = k > 16;
+  const int s = two ? lane : (lane & 15);
+  const bool live = s < k;
+  const int b = live ? T.cand(a, s) : a;
+  const int d_ab = live ? T.cdist(a, s) : 0;  // = euc2d(xa, xb), kept with the lists
+  const int2 xb = T.coord(b);
   int p, s1, s2 = -1, s3 = -1;
   if (do_or)
     T.walk(a, p, s1, s2, s3);
   else
     T.nbrs(a, p, s1);
   const int2 xa = T.coord(a), x1 = T.coord(s1), xp = T.coord(p);
-  const int d_as = euc2d(xa, x1), d_ap = euc2d(xp, xa);
-  // gains in 32 bits: each is a signed sum of at most six EUC_2D costs of
-  // coordinates below 2^24 (each cost below 2^25)
-  int32_t rem1 = 0, rem2 = 0, rem3 = 0;
   int2 x2 = xa, x3 = xa;
   if (do_or) {
     x2 = T.coord(s2);
     x3 = T.coord(s3);
+  }
+  // b's tour neighbour on this lane's side (pass 0), and for k > 16 the
+  // predecessor for pass 1
+  int bn0 = a, bn1 = a;
+  if (live) {
+    if (two)
+      T.nbrs(b, bn1, bn0);
+    else
+      bn0 = T.adj(b, lane < 16);
+  }
+  const int2 xbn0 = T.coord(bn0), xbn1 = two ? T.coord(bn1) : xa;
+  const int d_as = euc2d(xa, x1), d_ap = euc2d(xp, xa);
+  // gains in 32 bits: each is a signed sum of at most six EUC_2D costs of
+  // coordinates below 2^24 (each cost below 2^25)
+  int32_t rem1 = 0, rem2 = 0, rem3 = 0;
+  if (do_or) {
     rem1 = d_ap + d_as - euc2d(xp, x1);
     rem2 = d_ap + euc2d(x1, x2) - euc2d(xp, x2);
     rem3 = d_ap + euc2d(x2, x3) - euc2d(xp, x3);
   }
   int32_t b2 = 0, bo = 0;
   int i2 = INT_MAX, io = INT_MAX;
-  const int passes = k <= 16 ? 1 : 2;
+  const int passes = two ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
-    const int side = k <= 16 ? (lane >> 4) : pass;
-    const int s = k <= 16 ? (lane & 15) : lane;
+    const int side = two ? pass : (lane >> 4);
+    const int bn = pass == 0 ? bn0 : bn1;
+    const int2 xbn = pass == 0 ? xbn0 : xbn1;
     int32_t g = 0;
     int32_t lo = 0;
     int li = INT_MAX;
-    if (s < k) {
-      const int b = T.cand(a, s);
-      const int bn = side == 0 ? T.succ(b) : T.pred(b);
-      const int2 xb = T.coord(b), xbn = T.coord(bn);
-      const int d_ab = T.cdist(a, s);  // = euc2d(xa, xb), kept with the lists
+    if (live) {
       const int d_bbn = euc2d(xb, xbn);
       if (side == 0) {
         if (d_as > d_ab) g = d_as + d_bbn - d_ab - euc2d(x1, xbn);
@@ -252,26 +274,28 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
   }
   g2 = b2;
   go = bo;
+  // the winner's b and tour neighbour, from its lane (the side is uniform)
+  int side = 0, sw = 0;
   if (b2 > 0) {
-    const int side = i2 / k, s = i2 % k;
-    const int b = T.cand(a, s);
+    side = i2 / k;
+    sw = i2 % k;
+  } else if (bo > 0) {
+    const int rest = io >> 2;
+    side = (io >> 1) & 1;
+    sw = rest % k;
+  }
+  const int wl = two ? sw : side * 16 + sw;
+  const int bw = __shfl_sync(kFull, b, wl);
+  const int bnw = __shfl_sync(kFull, (two && side == 1) ? bn1 : bn0, wl);
+  if (b2 > 0) {
     if (side == 0) {
-      mv2[0] = a; mv2[1] = s1; mv2[2] = b; mv2[3] = T.succ(b);
+      mv2[0] = a; mv2[1] = s1; mv2[2] = bw; mv2[3] = bnw;
     } else {
-      mv2[0] = p; mv2[1] = a; mv2[2] = T.pred(b); mv2[3] = b;
+      mv2[0] = p; mv2[1] = a; mv2[2] = bnw; mv2[3] = bw;
     }
   } else if (bo > 0) {
-    const int kept = io & 1, side = (io >> 1) & 1, rest = io >> 2;
-    const int s = rest % k, l = rest / k + 1;
-    const int b = T.cand(a, s);
-    int u, v;
-    if (side == 0) {
-      u = b;
-      v = T.succ(b);
-    } else {
-      u = T.pred(b);
-      v = b;
-    }
+    const int kept = io & 1, l = (io >> 2) / k + 1;
+    const int u = side == 0 ? bw : bnw, v = side == 0 ? bnw : bw;
     mvo[0] = p; mvo[1] = a; mvo[2] = l == 1 ? a : (l == 2 ? s1 : s2);
     mvo[3] = l == 1 ? s1 : (l == 2 ? s2 : s3); mvo[4] = u; mvo[5] = v; mvo[6] = kept;
   }

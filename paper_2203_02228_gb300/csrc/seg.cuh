@@ -397,6 +397,19 @@ struct SegTour {
     int id = locate(q);
     return step_dn(q, id);
   }
+  // succ(q) when up, else pred(q): one lookup whatever the direction
+  __device__ __forceinline__ int adj(int q, bool up) const {
+    const int id = locate(q);
+    const Seg s = T.sg[id];
+    const int d = s.rev ? s.lo + s.len - 1 - q : q - s.lo;  // q's offset in ant order
+    if (up ? d < s.len - 1 : d > 0) return (up != (bool)s.rev) ? q + 1 : q - 1;
+    int r = T.rankA[id] + (up ? 1 : -1);
+    if (r == *T.S) r = 0;
+    if (r < 0) r = *T.S - 1;
+    const Seg t = T.sg[T.A[r]];
+    // first node in ant order of the next segment, or last of the previous
+    return (up == (bool)t.rev) ? t.lo + t.len - 1 : t.lo;
+  }
   __device__ __forceinline__ void nbrs(int q, int& p, int& s) const {
     const int id = locate(q);
     int i1 = id, i2 = id;
@@ -566,6 +579,7 @@ struct HybTour {
   __device__ __forceinline__ int pos_of(int x) const { return arrays() ? ar.pos_of(x) : sg.pos_of(x); }
   __device__ __forceinline__ int succ(int x) const { return arrays() ? ar.succ(x) : sg.succ(x); }
   __device__ __forceinline__ int pred(int x) const { return arrays() ? ar.pred(x) : sg.pred(x); }
+  __device__ __forceinline__ int adj(int x, bool up) const { return arrays() ? ar.adj(x, up) : sg.adj(x, up); }
   __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
     if (arrays())
       ar.nbrs(x, p, s);
