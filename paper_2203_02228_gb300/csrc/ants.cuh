@@ -251,12 +251,13 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
   // scan of the visited words that skips full ones
   const uint64_t t0 = global_ns();
   const int2 xu = C.XYsrc[pc];
-  const int near = ring_nearest(C.xy, C.grid, C.cell_start, C.cell_pts, xu, 24,
-                                [&](int v) { return vis_get(vis, C.src_pos[v]); });
+  int qn;
+  const int near = ring_nearest(C.cell_src, C.grid, C.cell_start, xu, 24,
+                                [&](const int4& P) { return vis_get(vis, P.x); }, qn);
   if (near >= 0) {
     W.global++;
     W.fall_ns += (int64_t)(global_ns() - t0);
-    return C.src_pos[near];
+    return qn;
   }
   uint64_t bk = ~0ull;
   int32_t bi = INT_MAX;

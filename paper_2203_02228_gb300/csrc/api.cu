@@ -44,6 +44,7 @@ struct faco_ctx {
   Grid grid{};                           // point grid (candidate lists, nearest unvisited)
   int32_t* cell_start = nullptr;
   int32_t* cell_pts = nullptr;
+  int4* cell_src = nullptr;
   Ants A{};
   std::vector<void*> ant_allocs;
   cudaGraphExec_t gexec = nullptr;       // whole iteration
@@ -111,6 +112,7 @@ Colony colony_view(const faco_ctx* c) {
   C.grid = c->grid;
   C.cell_start = c->cell_start;
   C.cell_pts = c->cell_pts;
+  C.cell_src = c->cell_src;
   C.tmp_route = c->tmp_route;
   C.tmp_pos = c->tmp_pos;
   return C;
@@ -260,13 +262,14 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     const int64_t cells = (int64_t)g.gx * g.gy;
     int32_t* cc = nullptr;
     if ((r2 = dalloc(tmp, &cc, cells)) != FACO_OK || (r2 = dalloc(c->allocs, &c->cell_start, cells + 1)) != FACO_OK ||
-        (r2 = dalloc(c->allocs, &c->cell_pts, n)) != FACO_OK) {
+        (r2 = dalloc(c->allocs, &c->cell_pts, n)) != FACO_OK || (r2 = dalloc(c->allocs, &c->cell_src, n)) != FACO_OK) {
       free_tmp();
       return r2;
     }
     c->grid = g;
     int32_t *cs = c->cell_start, *cp = c->cell_pts;
-    if (build_lists(c->xy, n, c->k, c->bl, g, cc, cs, cp, c->cand, c->backup, c->eta, c->dcand, s) != cudaSuccess) {
+    if (build_lists(c->xy, n, c->k, c->bl, g, cc, cs, cp, c->cell_src, c->cand, c->backup, c->eta, c->dcand, s) !=
+        cudaSuccess) {
       free_tmp();
       return FACO_E_CUDA;
     }
@@ -285,7 +288,7 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
       return r2;
     }
     cudaError_t e = launch_nn_tour(c->xy, n, c->cand, c->k, c->backup, c->bl, c->init_route, vis_g, g,
-                                   c->cell_start, c->cell_pts, s);
+                                   c->cell_start, c->cell_src, s);
     if (e == cudaSuccess) e = launch_positions(c->init_route, c->src_pos, n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fl, 0, n, s);
     if (e == cudaSuccess)

@@ -48,6 +48,10 @@ __device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
   const int2 xu = C.xy[u];
   C.XYsrc[p] = xu;
   C.Dsrc[p] = euc2d(xu, C.xy[pn]);
+  // the grid's point records, entry p, with the new source positions
+  const int v = C.cell_pts[p];
+  const int2 xv = C.xy[v];
+  C.cell_src[p] = make_int4(C.src_pos[v], xv.x, xv.y, v);
 }
 
 // Exclusive prefix sums of the source edge lengths (one block).

@@ -90,6 +90,8 @@ struct Colony {
   Grid grid;             // point grid of the candidate-list build
   const int32_t* cell_start;  // [cells+1]
   const int32_t* cell_pts;    // [n] node ids by cell
+  int4* cell_src;        // [n] the same points: (source position, x, y, node id); source positions
+                         //     refreshed with each iteration's rows
   int32_t* tmp_route;    // [n] iteration-best tour, materialised
   int32_t* tmp_pos;      // [n]
 };
@@ -100,6 +102,7 @@ struct ColonySetup {
   int32_t* cell_cnt;     // [cells] counts, then the fill cursor
   int32_t* cell_start;   // [cells+1]
   int32_t* cell_pts;     // [n]
+  int4* cell_src;        // [n] (node id, x, y, node id) until the first rows are written
   int32_t* cand;         // [n][k]
   int32_t* backup;       // [n][bl]
   float* eta;            // [n][k]

@@ -98,9 +98,13 @@ __global__ void __launch_bounds__(1024) k_scan_i32(int32_t* count, int32_t* star
   scan_i32_body(count, start, len, nullptr);
 }
 
-__global__ void k_cell_fill(const int2* xy, int n, Grid g, int32_t* cursor, int32_t* pts) {
+__global__ void k_cell_fill(const int2* xy, int n, Grid g, int32_t* cursor, int32_t* pts, int4* recs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) pts[atomicAdd(&cursor[cell_of(g, xy[i])], 1)] = i;
+  if (i >= n) return;
+  const int2 p = xy[i];
+  const int j = atomicAdd(&cursor[cell_of(g, p)], 1);
+  pts[j] = i;
+  if (recs) recs[j] = make_int4(i, p.x, p.y, i);
 }
 
 __device__ __forceinline__ void knn_body(const int2* xy, int n, const Grid& g, const int32_t* start,
@@ -229,7 +233,12 @@ __global__ void k_cell_fill_b(const Colony* cols, const ColonySetup* sets, const
   const int2 e = map[blockIdx.x];
   const int i = e.y * blockDim.x + threadIdx.x;
   const Colony C = cols[e.x];
-  if (i < C.n) sets[e.x].cell_pts[atomicAdd(&sets[e.x].cell_cnt[cell_of(C.grid, C.xy[i])], 1)] = i;
+  if (i >= C.n) return;
+  const ColonySetup& S = sets[e.x];
+  const int2 p = C.xy[i];
+  const int j = atomicAdd(&S.cell_cnt[cell_of(C.grid, p)], 1);
+  S.cell_pts[j] = i;
+  S.cell_src[j] = make_int4(i, p.x, p.y, i);
 }
 
 __global__ void __launch_bounds__(128) k_knn_b(const Colony* cols, const ColonySetup* sets, const int2* map) {
@@ -270,7 +279,7 @@ cudaError_t launch_bbox_check(const int2* xy, int n, int32_t* out5, cudaStream_t
 }
 
 cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int32_t* cell_count,
-                        int32_t* cell_start, int32_t* cell_pts, int32_t* cand, int32_t* backup,
+                        int32_t* cell_start, int32_t* cell_pts, int4* cell_src, int32_t* cand, int32_t* backup,
                         float* eta, int32_t* dcand, cudaStream_t s) {
   const int cells = g.gx * g.gy;
   cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * cells, s);
@@ -279,7 +288,7 @@ cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int
   k_scan_i32<<<1, 1024, 0, s>>>(cell_count, cell_start, cells);
   e = cudaMemcpyAsync(cell_count, cell_start, sizeof(int32_t) * cells, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
-  k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(xy, n, g, cell_count, cell_pts);
+  k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(xy, n, g, cell_count, cell_pts, cell_src);
   k_knn<<<(n + 127) / 128, 128, 0, s>>>(xy, n, g, cell_start, cell_pts, k, bl, cand, backup, eta, dcand);
   return cudaGetLastError();
 }

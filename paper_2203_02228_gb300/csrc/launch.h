@@ -58,7 +58,7 @@ cudaError_t launch_tour_length(const int2* xy, const int32_t* route, int n, int6
 // knn.cu
 cudaError_t launch_bbox_check(const int2* xy, int n, int32_t* out5, cudaStream_t s);
 cudaError_t build_lists(const int2* xy, int n, int k, int bl, const Grid& g, int32_t* cell_count,
-                        int32_t* cell_start, int32_t* cell_pts, int32_t* cand, int32_t* backup,
+                        int32_t* cell_start, int32_t* cell_pts, int4* cell_src, int32_t* cand, int32_t* backup,
                         float* eta, int32_t* dcand, cudaStream_t s);
 
 cudaError_t launch_grid_batch(Colony* cols, const ColonySetup* sets, int count, const int2* map256, int nmap256,
@@ -69,7 +69,7 @@ cudaError_t build_lists_batch(const Colony* cols, const ColonySetup* sets, int c
 // tour.cu
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
                            int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
-                           const int32_t* cpts, cudaStream_t s);
+                           const int4* recs, cudaStream_t s);
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
                            int verify, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s);

@@ -189,6 +189,10 @@ void group_layout(Group& g, char* base) {
     g.hS[i].cell_pts = B.take<int32_t>(g.n[i]);
     g.hC[i].cell_pts = g.hS[i].cell_pts;
   }
+  for (int i = 0; i < C; ++i) {
+    g.hS[i].cell_src = B.take<int4>(g.n[i]);
+    g.hC[i].cell_src = g.hS[i].cell_src;
+  }
   for (int i = 0; i < C; ++i) g.hS[i].init_route = B.take<int32_t>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hS[i].queue = B.take<int32_t>(g.n[i]);
   for (int i = 0; i < C; ++i) g.hS[i].logb = B.take<int32_t>(g.n[i]);

@@ -94,7 +94,7 @@ extern "C" int faco_lists_noalloc(const int32_t* coords_dev, int32_t n, int32_t 
   g.gy = (hb[3] - hb[1]) / g.cs + 1;
   if ((int64_t)g.gx * g.gy > kNoAllocMaxCells) return FACO_E_SIZE;
   // counts are cleared inside build_lists; starts and points are overwritten
-  if (build_lists(reinterpret_cast<const int2*>(coords_dev), n, ke, ble, g, counts, starts, pts, cand_dev,
+  if (build_lists(reinterpret_cast<const int2*>(coords_dev), n, ke, ble, g, counts, starts, pts, nullptr, cand_dev,
                   ble > 0 ? backup_dev : cand_dev, eta_dev, nullptr, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return FACO_E_CUDA;

@@ -19,7 +19,7 @@ namespace {
 
 __device__ __forceinline__ void nn_tour_body(const int2* xy, int n, const int32_t* cand, int k,
                                              const int32_t* backup, int bl, int32_t* route, uint32_t* vis,
-                                             const Grid& g, const int32_t* cstart, const int32_t* cpts) {
+                                             const Grid& g, const int32_t* cstart, const int4* recs) {
   const int lane = lane_id();
   const int words = (n + 31) >> 5;
   for (int i = lane; i < words; i += 32) vis[i] = 0;
@@ -49,8 +49,9 @@ __device__ __forceinline__ void nn_tour_body(const int2* xy, int n, const int32_
       // global nearest unvisited node: rings of grid cells, else a scan of
       // the visited words that skips full ones
       const int2 xu = xy[u];
-      v = ring_nearest(xy, g, cstart, cpts, xu, 24,
-                       [&](int x) { return ((vis[x >> 5] >> (x & 31)) & 1u) != 0; });
+      int h;
+      v = ring_nearest(recs, g, cstart, xu, 24,
+                       [&](const int4& P) { return ((vis[P.w >> 5] >> (P.w & 31)) & 1u) != 0; }, h);
     }
     if (v < 0) {
       const int2 xu = xy[u];
@@ -84,9 +85,9 @@ __device__ __forceinline__ void nn_tour_body(const int2* xy, int n, const int32_
 __global__ void __launch_bounds__(32) k_nn_tour(const int2* xy, int n, const int32_t* cand, int k,
                                                 const int32_t* backup, int bl, int32_t* route,
                                                 uint32_t* vis_g, Grid g, const int32_t* cstart,
-                                                const int32_t* cpts) {
+                                                const int4* recs) {
   extern __shared__ uint32_t sv[];
-  nn_tour_body(xy, n, cand, k, backup, bl, route, vis_g ? vis_g : sv, g, cstart, cpts);
+  nn_tour_body(xy, n, cand, k, backup, bl, route, vis_g ? vis_g : sv, g, cstart, recs);
 }
 
 // Batch: one warp per colony, visited bits in shared memory.
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(32) k_nn_tour_b(const Colony* cols, const Colo
   extern __shared__ uint32_t sv[];
   const Colony C = cols[blockIdx.x];
   const ColonySetup S = sets[blockIdx.x];
-  nn_tour_body(C.xy, C.n, S.cand, C.k, S.backup, C.bl, S.init_route, sv, C.grid, S.cell_start, S.cell_pts);
+  nn_tour_body(C.xy, C.n, S.cand, C.k, S.backup, C.bl, S.init_route, sv, C.grid, S.cell_start, S.cell_src);
 }
 
 // Positions reversed by one move (at most three flips): first position and
@@ -386,13 +387,13 @@ __global__ void k_tests(int what, const void* in, void* out, int count, int widt
 
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
                            int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
-                           const int32_t* cpts, cudaStream_t s) {
+                           const int4* recs, cudaStream_t s) {
   const size_t smem = vis_g ? 0 : (size_t)((n + 31) >> 5) * sizeof(uint32_t);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_nn_tour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g, g, cstart, cpts);
+  k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g, g, cstart, recs);
   return cudaGetLastError();
 }
 
