@@ -399,7 +399,7 @@ def main():
     ap.add_argument("--iters", type=int, default=0, help="override the iteration budget (testing only)")
     ap.add_argument("--sections", default="main,batch,serve", help="comma list of: main, batch, serve")
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2.0])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2.0, 8.0])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-pool-gb", type=int, default=64)
     args = ap.parse_args()

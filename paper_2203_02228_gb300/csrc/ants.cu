@@ -2,9 +2,32 @@
 // one-colony kernels (segment-table block per ant, then arrays for the ants
 // whose table filled up) and the batch segment-table kernel.  The batch
 // array kernel is instantiated in ants_arr_b.cu.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "ants.cuh"
 
 namespace faco {
+
+cudaError_t allow_dyn_smem(const void* f, size_t need) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  const size_t limit = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  if (need > limit) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(dev, f);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
 
 int ants_seg_cap_ls(int n, int seg_cap) {
   if (seg_cap <= 0) return 0;
@@ -66,14 +89,14 @@ size_t ants_blk_batch_smem(int kw) {
   const int threads = 32 * kAntWarps;
   int blocks = regs_sm / (fa.numRegs > 0 ? fa.numRegs * threads : threads);
   if (blocks < 1) blocks = 1;
+  if (allow_dyn_smem(f, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
   for (; blocks >= 1; --blocks) {
     long long S = (long long)smem_sm / blocks - reserved - (long long)fa.sharedSizeBytes;
     S &= ~127LL;
     for (int tries = 0; tries < 8 && S > 0; ++tries, S -= 256) {
-      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S) != cudaSuccess) {
-        (void)cudaGetLastError();
-        continue;
-      }
       int nb = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, (size_t)S) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -119,7 +142,7 @@ int ants_batch_resident(int variant, int kw, size_t smem) {
 cudaError_t prepare_ants_batch(int kw, size_t smem_blk, size_t smem_arr) {
   const void* f = kw == 16 ? reinterpret_cast<const void*>(k_ants_blk_b<16>)
                            : reinterpret_cast<const void*>(k_ants_blk_b<32>);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk);
+  cudaError_t e = allow_dyn_smem(f, smem_blk);
   if (e == cudaSuccess) e = prepare_ants_arr_batch_2(kw, smem_arr);
   if (e == cudaSuccess) e = prepare_ants_arr_batch_4(kw, smem_arr);
   if (e == cudaSuccess) e = prepare_ants_arr_batch_8(kw, smem_arr);
@@ -129,13 +152,11 @@ cudaError_t prepare_ants_batch(int kw, size_t smem_blk, size_t smem_arr) {
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr) {
   cudaError_t e;
   if (kw == 16) {
-    e = cudaFuncSetAttribute(k_ants_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_ants<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+    e = allow_dyn_smem(reinterpret_cast<const void*>(k_ants_blk<16>), smem_seg);
+    if (e == cudaSuccess) e = allow_dyn_smem(reinterpret_cast<const void*>(k_ants<16, false>), smem_arr);
   } else {
-    e = cudaFuncSetAttribute(k_ants_blk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_seg);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_ants<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_arr);
+    e = allow_dyn_smem(reinterpret_cast<const void*>(k_ants_blk<32>), smem_seg);
+    if (e == cudaSuccess) e = allow_dyn_smem(reinterpret_cast<const void*>(k_ants<32, false>), smem_arr);
   }
   return e;
 }

@@ -28,7 +28,7 @@ template <int MB>
 cudaError_t prepare_arr_b_mb(int kw, size_t smem) {
   const void* f = kw == 16 ? reinterpret_cast<const void*>(k_ants_b<16, MB>)
                            : reinterpret_cast<const void*>(k_ants_b<32, MB>);
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return allow_dyn_smem(f, smem);
 }
 
 template <int MB>

@@ -11,6 +11,12 @@ namespace faco {
 // ants.cu
 cudaError_t launch_ants(const Colony& C, const Ants& A, cudaStream_t s);
 cudaError_t prepare_ants_kernel(int kw, size_t smem_seg, size_t smem_arr);
+// Lets kernel f take as much dynamic shared memory as the device allows
+// beside its static shared memory.  Set once per kernel and device and
+// never lowered, so a launch stays valid whoever prepared the kernel last
+// (colonies, batches and a server's cohorts share the kernels, from any
+// host thread).  cudaErrorInvalidValue if `need` bytes exceed that limit.
+cudaError_t allow_dyn_smem(const void* f, size_t need);
 size_t ants_smem_per_warp(int n, int seg_cap, bool segs);
 // Segments per ant table during the local search (the visited bits' room added).
 int ants_seg_cap_ls(int n, int seg_cap);

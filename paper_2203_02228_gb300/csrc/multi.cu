@@ -364,14 +364,17 @@ int Runner::build(const std::vector<RunEntry>& entries, size_t smem, cudaStream_
   B.take<int2>((size_t)redo_cap);
   B.take<int32_t>(1);
   if (B.size > mem_bytes) {
+    // a runner rebuilt for changing sets (the server's cohorts) grows
+    // geometrically: a free waits for the whole device
+    const size_t want = mem_bytes ? std::max(B.size, 2 * mem_bytes) : B.size;
     if (mem) {
       CK(cudaStreamSynchronize(s));
       cudaFree(mem);
       mem = nullptr;
       mem_bytes = 0;
     }
-    CK(cudaMalloc(&mem, B.size));
-    mem_bytes = B.size;
+    CK(cudaMalloc(&mem, want));
+    mem_bytes = want;
   }
   Bump D(mem);
   dC = D.take<Colony>(C);

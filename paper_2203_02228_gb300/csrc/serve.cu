@@ -1,8 +1,11 @@
 // serve.cu -- the request server of include/faco_serve.h: admission by a
 // device-memory pool, per-request set-up on a side stream, continuous
-// iteration rounds over every active request (the batch launches of
-// multi.h), results to pinned host memory.  The scheduler is a host thread;
-// every step of the method runs in the library's kernels.
+// iteration rounds (the batch launches of multi.h), results to pinned host
+// memory.  Active requests are grouped into cohorts by roulette width and
+// size; each cohort iterates in rounds of its own on a stream of its own,
+// so a small request is not held to the pace of a large one and the
+// cohorts' kernels share the GPU.  The scheduler is a host thread; every
+// step of the method runs in the library's kernels.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -92,7 +95,7 @@ struct Request {
   AntSet a;
   char* block = nullptr;
   size_t bytes = 0;
-  int iters = 0, variant = kVarArr8;
+  int iters = 0, variant = kVarArr8, cohort = 0;
   cudaEvent_t ev = nullptr;  // set-up complete, later: result copied
   char* pinned = nullptr;    // tour (n int32), length (int64), error flags (int32)
   std::vector<int32_t> tour;
@@ -112,11 +115,16 @@ int plan_request(Request& r, const faco_params& prm, size_t smem_blk) {
 
 }  // namespace
 
+// Cohorts: roulette width (16, 32) x size (n <= 4096, <= 32768, larger).
+constexpr int kSizeBuckets = 3;
+constexpr int kCohorts = 2 * kSizeBuckets;
+
 struct faco_server {
   faco_params prm{};
   int device = 0;
   size_t smem_blk[2] = {0, 0};  // roulette width 16, 32
-  cudaStream_t compute = nullptr, setup = nullptr;
+  cudaStream_t setup = nullptr;
+  cudaStream_t lane[kCohorts] = {};  // each cohort's rounds and result copies
   char* pool_mem = nullptr;
   Pool pool;
   std::mutex mu;
@@ -127,12 +135,12 @@ struct faco_server {
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
   std::deque<Request*> queue;
   // owned by the scheduler thread
-  std::vector<Request*> setting, active[2], finishing;
-  Runner runner[2];
-  bool dirty[2] = {true, true};
-  cudaEvent_t round_ev[2] = {nullptr, nullptr};
-  bool round_pending[2] = {false, false};
-  int round_par = 0;
+  std::vector<Request*> setting, active[kCohorts], finishing;
+  Runner runner[kCohorts];
+  bool dirty[kCohorts] = {true, true, true, true, true, true};
+  cudaEvent_t round_ev[kCohorts][2] = {};
+  bool round_pending[kCohorts][2] = {};
+  int round_par[kCohorts] = {};
   faco_server_stats stats{};
 };
 
@@ -148,6 +156,11 @@ namespace {
   } while (0)
 
 int wslot(const Request* r) { return r->g.kw == 32 ? 1 : 0; }
+
+int cohort_of(const Request* r) {
+  const int b = r->n <= 4096 ? 0 : (r->n <= 32768 ? 1 : 2);
+  return wslot(r) * kSizeBuckets + b;
+}
 
 // Marks r done with `status` and returns its memory (scheduler thread).
 void finish(faco_server* s, Request* r, int status) {
@@ -168,6 +181,7 @@ void finish(faco_server* s, Request* r, int status) {
 }
 
 int start_setup(faco_server* s, Request* r) {
+  r->cohort = cohort_of(r);
   char* base = r->block;
   group_layout(r->g, base);
   const size_t gb = (r->g.bytes + 255) & ~(size_t)255;
@@ -199,9 +213,10 @@ int choose_variant(faco_server* s, Request* r) {
   int v = tuner_get(cls, r->ants, r->g.kw);
   if (v < 0) {
     std::vector<RunEntry> e{RunEntry{&r->g, 0, &r->a, kVarArr8}};
-    int rc = tuner_run(e, s->smem_blk[wslot(r)], s->compute);
+    cudaStream_t st = s->lane[r->cohort];
+    int rc = tuner_run(e, s->smem_blk[wslot(r)], st);
     if (rc != FACO_OK) return rc;
-    rc = antset_zero(r->a, s->compute);  // counters of the trial launches
+    rc = antset_zero(r->a, st);  // counters of the trial launches
     if (rc != FACO_OK) return rc;
     v = tuner_get(cls, r->ants, r->g.kw);
   }
@@ -212,75 +227,81 @@ int choose_variant(faco_server* s, Request* r) {
 
 int enqueue_result_copy(faco_server* s, Request* r) {
   const Colony& C = r->g.hC[0];
-  CKS(cudaMemcpyAsync(r->pinned, C.gb_route, sizeof(int32_t) * (size_t)r->n, cudaMemcpyDeviceToHost, s->compute));
+  cudaStream_t st = s->lane[r->cohort];
+  CKS(cudaMemcpyAsync(r->pinned, C.gb_route, sizeof(int32_t) * (size_t)r->n, cudaMemcpyDeviceToHost, st));
   char* tail = r->pinned + sizeof(int32_t) * (size_t)r->n;
   CKS(cudaMemcpyAsync(tail, reinterpret_cast<char*>(C.st) + offsetof(DevState, gb_len), sizeof(int64_t),
-                      cudaMemcpyDeviceToHost, s->compute));
+                      cudaMemcpyDeviceToHost, st));
   CKS(cudaMemcpyAsync(tail + 8, reinterpret_cast<char*>(C.st) + offsetof(DevState, error), sizeof(int32_t),
-                      cudaMemcpyDeviceToHost, s->compute));
-  CKS(cudaEventRecord(r->ev, s->compute));
+                      cudaMemcpyDeviceToHost, st));
+  CKS(cudaEventRecord(r->ev, st));
   return FACO_OK;
 }
 
-// One iteration of every active request; requests whose budget is spent
-// leave with their result copy in flight.
-int run_round(faco_server* s) {
-  bool any = false;
-  for (int w = 0; w < 2; ++w) {
-    std::vector<Request*>& act = s->active[w];
-    if (act.empty()) continue;
-    any = true;
-    if (s->dirty[w]) {
-      int rc = s->runner[w].build(entries(act), s->smem_blk[w], s->compute);
-      if (rc != FACO_OK) return rc;
-      s->dirty[w] = false;
-    }
-    int rc = s->runner[w].enqueue(s->compute, 3);
-    if (rc != FACO_OK) return rc;
-    s->stats.kernel_launches += s->runner[w].kernels_per_iteration();
-  }
-  if (!any) return FACO_OK;
-  s->stats.rounds++;
+// One iteration of every active request of each cohort that has fewer than
+// two rounds in flight; requests whose budget is spent leave with their
+// result copy in flight.  *queued: some cohort got a round.
+int run_rounds(faco_server* s, bool* queued) {
   int64_t nact = 0;
-  for (int w = 0; w < 2; ++w) {
-    std::vector<Request*>& act = s->active[w];
-    nact += (int64_t)act.size();
+  for (int c = 0; c < kCohorts; ++c) nact += (int64_t)s->active[c].size();
+  if (nact > s->stats.peak_active) s->stats.peak_active = nact;
+  for (int c = 0; c < kCohorts; ++c) {
+    std::vector<Request*>& act = s->active[c];
+    if (act.empty()) continue;
+    // the cohort's round before last must be done before another is queued:
+    // the host stays at most one round ahead of the GPU
+    const int p = s->round_par[c];
+    if (s->round_pending[c][p]) {
+      const cudaError_t q = cudaEventQuery(s->round_ev[c][p]);
+      if (q == cudaErrorNotReady) continue;
+      CKS(q);
+      s->round_pending[c][p] = false;
+    }
+    *queued = true;
+    cudaStream_t st = s->lane[c];
+    if (s->dirty[c]) {
+      int rc = s->runner[c].build(entries(act), s->smem_blk[c / kSizeBuckets], st);
+      if (rc != FACO_OK) return rc;
+      s->dirty[c] = false;
+    }
+    int rc = s->runner[c].enqueue(st, 3);
+    if (rc != FACO_OK) return rc;
+    s->stats.kernel_launches += s->runner[c].kernels_per_iteration();
+    s->stats.rounds++;
     std::vector<Request*> keep;
     for (Request* r : act) {
       if (++r->iters < r->budget) {
         keep.push_back(r);
         continue;
       }
-      int rc = enqueue_result_copy(s, r);
+      rc = enqueue_result_copy(s, r);
       if (rc != FACO_OK) return rc;
       r->st = St::Finishing;
       s->finishing.push_back(r);
-      s->dirty[w] = true;
+      s->dirty[c] = true;
     }
     act.swap(keep);
+    CKS(cudaEventRecord(s->round_ev[c][p], st));
+    s->round_pending[c][p] = true;
+    s->round_par[c] = p ^ 1;
   }
-  if (nact > s->stats.peak_active) s->stats.peak_active = nact;
-  // at most two rounds in flight: the host stays one round ahead of the GPU
-  const int p = s->round_par;
-  CKS(cudaEventRecord(s->round_ev[p], s->compute));
-  if (s->round_pending[p ^ 1]) CKS(cudaEventSynchronize(s->round_ev[p ^ 1]));
-  s->round_pending[p ^ 1] = false;
-  s->round_pending[p] = true;
-  s->round_par = p ^ 1;
   return FACO_OK;
 }
 
 void fail_all(faco_server* s, int status) {
   std::vector<Request*> all;
   for (Request* r : s->setting) all.push_back(r);
-  for (int w = 0; w < 2; ++w)
-    for (Request* r : s->active[w]) all.push_back(r);
+  for (int c = 0; c < kCohorts; ++c)
+    for (Request* r : s->active[c]) all.push_back(r);
   for (Request* r : s->finishing) all.push_back(r);
   s->setting.clear();
-  s->active[0].clear();
-  s->active[1].clear();
+  for (int c = 0; c < kCohorts; ++c) {
+    s->active[c].clear();
+    s->dirty[c] = true;
+    s->round_pending[c][0] = s->round_pending[c][1] = false;
+  }
   s->finishing.clear();
-  cudaStreamSynchronize(s->compute);
+  for (int c = 0; c < kCohorts; ++c) cudaStreamSynchronize(s->lane[c]);
   cudaStreamSynchronize(s->setup);
   (void)cudaGetLastError();
   for (Request* r : all) finish(s, r, status);
@@ -292,8 +313,8 @@ void scheduler(faco_server* s) {
     std::vector<Request*> admit;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      const bool busy = !s->setting.empty() || !s->active[0].empty() || !s->active[1].empty() ||
-                        !s->finishing.empty();
+      bool busy = !s->setting.empty() || !s->finishing.empty();
+      for (int c = 0; c < kCohorts; ++c) busy = busy || !s->active[c].empty();
       if (!busy && s->queue.empty()) {
         if (s->stop) break;
         s->cv.wait_for(lk, std::chrono::milliseconds(5));
@@ -332,10 +353,11 @@ void scheduler(faco_server* s) {
         continue;
       }
       r->st = St::Active;
-      s->active[wslot(r)].push_back(r);
-      s->dirty[wslot(r)] = true;
+      s->active[r->cohort].push_back(r);
+      s->dirty[r->cohort] = true;
     }
-    const int rc = run_round(s);
+    bool queued = false;
+    const int rc = run_rounds(s, &queued);
     if (rc != FACO_OK) {
       fail_all(s, rc);
       continue;
@@ -361,8 +383,9 @@ void scheduler(faco_server* s) {
       (void)cudaGetLastError();
       finish(s, r, st);
     }
-    if (s->active[0].empty() && s->active[1].empty() && (!s->setting.empty() || !s->finishing.empty()))
-      std::this_thread::sleep_for(std::chrono::microseconds(100));
+    // nothing queued this pass (every cohort two rounds ahead, or only
+    // set-ups and result copies in flight): let the GPU catch up
+    if (!queued) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
 
@@ -407,10 +430,12 @@ int faco_server_create(size_t device_bytes, const faco_params* p, faco_server** 
     CKS(cudaGetDevice(&s->device));
     s->smem_blk[0] = batch_smem_blk(16);
     s->smem_blk[1] = batch_smem_blk(32);
-    CKS(cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking));
     CKS(cudaStreamCreateWithFlags(&s->setup, cudaStreamNonBlocking));
-    CKS(cudaEventCreateWithFlags(&s->round_ev[0], cudaEventDisableTiming));
-    CKS(cudaEventCreateWithFlags(&s->round_ev[1], cudaEventDisableTiming));
+    for (int c = 0; c < kCohorts; ++c) {
+      CKS(cudaStreamCreateWithFlags(&s->lane[c], cudaStreamNonBlocking));
+      CKS(cudaEventCreateWithFlags(&s->round_ev[c][0], cudaEventDisableTiming));
+      CKS(cudaEventCreateWithFlags(&s->round_ev[c][1], cudaEventDisableTiming));
+    }
     CKS(cudaMalloc(&s->pool_mem, device_bytes));
     s->pool.init(s->pool_mem, device_bytes);
     s->stats.pool_bytes = (int64_t)s->pool.size();
@@ -418,9 +443,11 @@ int faco_server_create(size_t device_bytes, const faco_params* p, faco_server** 
   }();
   if (rc != FACO_OK) {
     if (s->pool_mem) cudaFree(s->pool_mem);
-    for (cudaEvent_t e : s->round_ev)
-      if (e) cudaEventDestroy(e);
-    if (s->compute) cudaStreamDestroy(s->compute);
+    for (int c = 0; c < kCohorts; ++c) {
+      for (cudaEvent_t e : s->round_ev[c])
+        if (e) cudaEventDestroy(e);
+      if (s->lane[c]) cudaStreamDestroy(s->lane[c]);
+    }
     if (s->setup) cudaStreamDestroy(s->setup);
     delete s;
     return rc;
@@ -531,7 +558,7 @@ void faco_server_destroy(faco_server* s) {
     s->cv.notify_all();
   }
   if (s->thr.joinable()) s->thr.join();
-  cudaStreamSynchronize(s->compute);
+  for (int c = 0; c < kCohorts; ++c) cudaStreamSynchronize(s->lane[c]);
   cudaStreamSynchronize(s->setup);
   for (auto& kv : s->reqs) {
     Request* r = kv.second.get();
@@ -539,10 +566,12 @@ void faco_server_destroy(faco_server* s) {
     if (r->pinned) cudaFreeHost(r->pinned);
   }
   s->reqs.clear();
-  for (cudaEvent_t e : s->round_ev)
-    if (e) cudaEventDestroy(e);
+  for (int c = 0; c < kCohorts; ++c) {
+    for (cudaEvent_t e : s->round_ev[c])
+      if (e) cudaEventDestroy(e);
+  }
   if (s->pool_mem) cudaFree(s->pool_mem);
-  cudaStreamDestroy(s->compute);
+  for (int c = 0; c < kCohorts; ++c) cudaStreamDestroy(s->lane[c]);
   cudaStreamDestroy(s->setup);
   delete s;
 }

@@ -390,7 +390,7 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
                            const int4* recs, cudaStream_t s) {
   const size_t smem = vis_g ? 0 : (size_t)((n + 31) >> 5) * sizeof(uint32_t);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_nn_tour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem(reinterpret_cast<const void*>(k_nn_tour), smem);
     if (e != cudaSuccess) return e;
   }
   k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g, g, cstart, recs);
@@ -409,7 +409,7 @@ cudaError_t launch_init_tour_batch(const Colony* cols, const ColonySetup* sets, 
   if (stage == 0) {
     const size_t smem = (size_t)((max_n + 31) >> 5) * sizeof(uint32_t);
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_nn_tour_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = allow_dyn_smem(reinterpret_cast<const void*>(k_nn_tour_b), smem);
       if (e != cudaSuccess) return e;
     }
     k_nn_tour_b<<<count, 32, smem, s>>>(cols, sets);
