@@ -290,7 +290,9 @@ def bench_batched(args, stream, flush, barrier):
         "speedup_vs_plain": inst_batch / inst_plain,
         "equal_results_on_sample": bool(same),
         "mean_best_length": float(np.mean(lens)),
-        "plan": {"segment_table_colonies": int((plan == 0).sum()), "array_colonies": int((plan == 1).sum())},
+        "plan": {"colonies_per_kernel": {name: int((plan == v).sum()) for v, name in
+                                         enumerate(("segment_table", "arrays_2_blocks_per_sm", "arrays_4_blocks_per_sm",
+                                                    "arrays_8_blocks_per_sm"))}},
         "gpu_launches_per_batch": int(launches), "graph_launches_per_batch": 1, "cpu_baseline": cpu,
         "h2d_bytes_per_batch": int(8 * ns.sum()), "d2h_bytes_per_batch": int(4 * ns.sum() + 8 * len(xs)),
     }

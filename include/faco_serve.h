@@ -12,9 +12,13 @@
  *   - an admitted request's set-up (candidate lists, initial tour and its
  *     local search, Alg 2 set-up) runs on a set-up stream while the GPU
  *     keeps iterating the active requests;
- *   - each round is one iteration (Alg 2 main loop body) of every active
- *     request, with the same launches as a faco_batch; a request joins at
- *     the next round after its set-up completes and leaves the round in
+ *   - active requests are grouped into cohorts by roulette width (k <= 16
+ *     or not) and size (n <= 4096, <= 32768, larger); each cohort iterates
+ *     in rounds of its own on a stream of its own, so cohorts proceed at
+ *     their own pace and their kernels share the GPU;
+ *   - a round is one iteration (Alg 2 main loop body) of every request of
+ *     the cohort, with the same launches as a faco_batch; a request joins
+ *     at the next round after its set-up completes and leaves the round in
  *     which its budget is spent;
  *   - its global-best tour and length are then copied to host memory and
  *     its device memory returns to the pool.
@@ -46,8 +50,8 @@ typedef struct {
   int64_t queued;          /* waiting for memory                                */
   int64_t setting_up;      /* admitted, set-up in flight                        */
   int64_t active;          /* iterating                                         */
-  int64_t peak_active;     /* largest number of requests in one round           */
-  int64_t rounds;          /* iteration rounds run                              */
+  int64_t peak_active;     /* largest number of requests iterating at once      */
+  int64_t rounds;          /* iteration rounds run (all cohorts)                */
   int64_t kernel_launches; /* kernels launched by the server so far             */
   int64_t pool_bytes;      /* device bytes of the pool                          */
   int64_t pool_in_use;     /* bytes held by admitted requests                   */

@@ -316,7 +316,8 @@ class Batch:
 
 class Server:
     """Request server (include/faco_serve.h): instances admitted by device
-    memory, set up while others iterate, iterated in shared rounds.
+    memory, set up while others iterate, iterated in rounds shared with the
+    requests of their cohort (roulette width and size class).
 
     A request's tour and length equal those of a Colony with the server's
     parameters and the request's seed, alone or in any mix.
