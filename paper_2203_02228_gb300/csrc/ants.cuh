@@ -265,14 +265,30 @@ __device__ __noinline__ int fallback_pick(const Colony& C, const uint32_t* vis, 
   for (int wi = lane; wi < words; wi += 32) {
     uint32_t fr = ~vis[wi];
     if (wi == words - 1 && (n & 31)) fr &= (1u << (n & 31)) - 1u;
-    while (fr) {
-      const int q = wi * 32 + __ffs(fr) - 1;
+    while (fr) {  // two unvisited positions of the word in flight
+      const int q0 = wi * 32 + __ffs(fr) - 1;
       fr &= fr - 1;
-      const uint64_t m = sqdist(xu, C.XYsrc[q]);
-      const int32_t node = C.src_route[q];
-      if (m < bk || (m == bk && node < bi)) {
-        bk = m;
-        bi = node;
+      int q1 = -1;
+      if (fr) {
+        q1 = wi * 32 + __ffs(fr) - 1;
+        fr &= fr - 1;
+      }
+      const int2 x0 = C.XYsrc[q0];
+      const int32_t n0 = C.src_route[q0];
+      int2 x1 = x0;
+      int32_t n1 = n0;
+      if (q1 >= 0) {
+        x1 = C.XYsrc[q1];
+        n1 = C.src_route[q1];
+      }
+      const uint64_t m0 = sqdist(xu, x0), m1 = sqdist(xu, x1);
+      if (m0 < bk || (m0 == bk && n0 < bi)) {
+        bk = m0;
+        bi = n0;
+      }
+      if (m1 < bk || (m1 == bk && n1 < bi)) {
+        bk = m1;
+        bi = n1;
       }
     }
   }

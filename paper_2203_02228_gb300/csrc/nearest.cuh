@@ -65,22 +65,30 @@ __device__ __forceinline__ int ring_nearest(const int4* recs, const Grid& g, con
       }
       const int total = __shfl_sync(kFull, incl, 31);
       const int excl_st = st - (incl - len);  // record index = excl_st(owner) + t
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        // owner lane of point t: the first lane whose inclusive sum exceeds t
-        int o = 0;
+      // two points per lane in flight: the record loads of a step do not
+      // wait for each other
+      constexpr int U = 2;
+      for (int t0 = 0; t0 < total; t0 += 32 * U) {
+        int4 P[U];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (__shfl_sync(kFull, incl, o + step - 1) <= t) o += step;
-        const int base = __shfl_sync(kFull, excl_st, o);
-        if (t < total) {
-          const int4 P = recs[base + t];
-          if (!visited(P)) {
-            const uint64_t m = sqdist(xu, make_int2(P.y, P.z));
-            if (m < bk || (m == bk && P.w < bi)) {
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + 32 * u + lane;
+          // owner lane of point t: the first lane whose inclusive sum exceeds t
+          int o = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (__shfl_sync(kFull, incl, o + step - 1) <= t) o += step;
+          const int base = __shfl_sync(kFull, excl_st, o);
+          P[u] = t < total ? recs[base + t] : make_int4(-1, 0, 0, INT_MAX);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (P[u].x >= 0 && !visited(P[u])) {
+            const uint64_t m = sqdist(xu, make_int2(P[u].y, P[u].z));
+            if (m < bk || (m == bk && P[u].w < bi)) {
               bk = m;
-              bi = P.w;
-              bh = P.x;
+              bi = P[u].w;
+              bh = P[u].x;
             }
           }
         }
