@@ -258,6 +258,11 @@ __device__ __forceinline__ int64_t shfl64_up(int64_t v, int o) {
   return (int64_t)__shfl_up_sync(kFull, (unsigned long long)v, o);
 }
 
+// Starts bringing the cache line holding p into L1 (no value returned).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Lexicographic minimum of (key, idx) over the warp, for idx >= 0; every
 // lane gets it.  Three warp reductions: the key's high word, its low word
 // among the lanes with that high word, the index among the lanes with that

@@ -34,6 +34,9 @@ __device__ __forceinline__ void nn_tour_body(const int2* xy, int n, const int32_
     int v = -1;
     {
       const int c = lane < k ? cand[(size_t)u * k + lane] : -1;
+      // the next node is most often one of these: their own lists start on
+      // their way to L1 now, off the chain of dependent steps
+      if (c >= 0) prefetch_l1(cand + (size_t)c * k);
       const bool ok = c >= 0 && !((vis[c >> 5] >> (c & 31)) & 1u);
       const unsigned bal = __ballot_sync(kFull, ok);
       if (bal) v = __shfl_sync(kFull, c, __ffs(bal) - 1);
