@@ -15,79 +15,107 @@ namespace {
 //   tau' = max(tau_min, min(tau_max, fmaf(rho, tau, delta * [edge in source])))
 //   Wsrc[p][s] = tau' * eta,  Csrc[p][s] = source position of cand[u][s].
 // update = 0 only sets tau = tau_max (Alg 2 set-up).
-__device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
+// Entry s of row p (s < kw).
+__device__ __forceinline__ void rows_entry(const Colony& C, int p, int s, int update) {
+  const int n = C.n, k = C.k, kw = C.kw;
+  const size_t o = (size_t)p * kw + s;
+  if (s >= k) {
+    C.Wsrc[o] = 0.0f;
+    C.Csrc[o] = -1;
+    C.Dcsrc[o] = 0;
+    return;
+  }
+  const int u = C.src_route[p];
+  const size_t idx = (size_t)u * k + s;
+  const int v = C.cand[idx];
+  float t;
+  if (update) {
+    const int pn = C.src_route[p + 1 == n ? 0 : p + 1];
+    const int pp = C.src_route[p == 0 ? n - 1 : p - 1];
+    const float tmax = C.st->tmax, tmin = C.st->tmin, delta = C.st->delta;
+    const float dep = (v == pn || v == pp) ? delta : 0.0f;
+    t = __fmaf_rn(C.rho, C.tau[idx], dep);
+    t = t < tmax ? t : tmax;
+    t = t > tmin ? t : tmin;
+  } else {
+    t = C.st->tmax;
+  }
+  C.tau[idx] = t;
+  C.Wsrc[o] = __fmul_rn(t, C.eta[idx]);
+  C.Csrc[o] = C.src_pos[v];
+  C.Dcsrc[o] = C.dcand[idx];
+}
+
+// The per-node parts of row p: coordinates, source edge length, and the
+// grid's point record p with the new source positions.
+__device__ __forceinline__ void rows_node(const Colony& C, int p) {
   const int n = C.n;
-  if (p >= n) return;
   const int u = C.src_route[p];
   const int pn = C.src_route[p + 1 == n ? 0 : p + 1];
-  const int pp = C.src_route[p == 0 ? n - 1 : p - 1];
-  const float tmax = C.st->tmax, tmin = C.st->tmin, delta = C.st->delta;
-  const int k = C.k, kw = C.kw;
-  for (int s = 0; s < k; ++s) {
-    const size_t idx = (size_t)u * k + s;
-    const int v = C.cand[idx];
-    float t;
-    if (update) {
-      const float dep = (v == pn || v == pp) ? delta : 0.0f;
-      t = __fmaf_rn(C.rho, C.tau[idx], dep);
-      t = t < tmax ? t : tmax;
-      t = t > tmin ? t : tmin;
-    } else {
-      t = tmax;
-    }
-    C.tau[idx] = t;
-    C.Wsrc[(size_t)p * kw + s] = __fmul_rn(t, C.eta[idx]);
-    C.Csrc[(size_t)p * kw + s] = C.src_pos[v];
-    C.Dcsrc[(size_t)p * kw + s] = C.dcand[idx];
-  }
-  for (int s = k; s < kw; ++s) {
-    C.Wsrc[(size_t)p * kw + s] = 0.0f;
-    C.Csrc[(size_t)p * kw + s] = -1;
-    C.Dcsrc[(size_t)p * kw + s] = 0;
-  }
   const int2 xu = C.xy[u];
   C.XYsrc[p] = xu;
   C.Dsrc[p] = euc2d(xu, C.xy[pn]);
-  // the grid's point records, entry p, with the new source positions
   const int v = C.cell_pts[p];
   const int2 xv = C.xy[v];
   C.cell_src[p] = make_int4(C.src_pos[v], xv.x, xv.y, v);
 }
 
+__device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
+  if (p >= C.n) return;
+  for (int s = 0; s < C.kw; ++s) rows_entry(C, p, s, update);
+  rows_node(C, p);
+}
+
 // Exclusive prefix sums of the source edge lengths (one block).
 __device__ __forceinline__ void scan_P_body(const Colony& C) {
+  // tiles of 8 consecutive edges per thread, read and written coalesced,
+  // with the running total carried from tile to tile
+  constexpr int E = 8;
   __shared__ int64_t warp_tot[32];
+  __shared__ int64_t s_carry;
   const int n = C.n, t = threadIdx.x, T = blockDim.x;
-  const int chunk = (n + T - 1) / T;
-  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
-  int64_t s = 0;
-  for (int i = lo; i < hi; ++i) s += C.Dsrc[i];
-  // block exclusive scan of s
-  const int lane = t & 31, w = t >> 5;
-  int64_t incl = s;
+  const int lane = t & 31, w = t >> 5, nw = T >> 5;
+  if (t == 0) s_carry = 0;
+  for (int base = 0; base < n; base += E * T) {
+    const int i0 = base + E * t;
+    int d[E];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = shfl64_up(incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_tot[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    int64_t v = lane < (T >> 5) ? warp_tot[lane] : 0;
+    for (int u = 0; u < E; ++u) d[u] = i0 + u < n ? C.Dsrc[i0 + u] : 0;
+    int64_t s = 0;
+#pragma unroll
+    for (int u = 0; u < E; ++u) s += d[u];
+    // block inclusive scan of s
+    int64_t incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = shfl64_up(v, o);
-      if (lane >= o) v += y;
+      const int64_t y = shfl64_up(incl, o);
+      if (lane >= o) incl += y;
     }
-    warp_tot[lane] = v;  // inclusive over warps
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int64_t v = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = shfl64_up(v, o);
+        if (lane >= o) v += y;
+      }
+      warp_tot[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t carry = s_carry;
+    int64_t run = carry + (incl - s) + (w > 0 ? warp_tot[w - 1] : 0);
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (i0 + u < n) C.Psrc[i0 + u] = run;
+      run += d[u];
+    }
+    const int64_t tile = warp_tot[nw - 1];
+    __syncthreads();  // every thread has read the carry and the warp totals
+    if (t == 0) s_carry = carry + tile;
   }
   __syncthreads();
-  int64_t run = (incl - s) + (w > 0 ? warp_tot[w - 1] : 0);
-  for (int i = lo; i < hi; ++i) {
-    C.Psrc[i] = run;
-    run += C.Dsrc[i];
-  }
-  if (t == T - 1) C.Psrc[n] = warp_tot[(T >> 5) - 1];
+  if (t == 0) C.Psrc[n] = s_carry;
 }
 
 __device__ __forceinline__ void set_limits(const Colony& C, DevState* st, int64_t L) {
@@ -238,7 +266,14 @@ __device__ __forceinline__ void state_init_body(const Colony& C, const int64_t* 
 // Kernels of one colony (descriptor by value) and of a batch (each block
 // reads its colony, and its block within the colony, from a block map).
 // ---------------------------------------------------------------------
-__global__ void k_rows(Colony C, int update) { rows_body(C, blockIdx.x * blockDim.x + threadIdx.x, update); }
+// A thread per row entry: consecutive threads write consecutive entries.
+__global__ void k_rows(Colony C, int update) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(t / C.kw), s = (int)(t % C.kw);
+  if (p >= C.n) return;
+  rows_entry(C, p, s, update);
+  if (s == 0) rows_node(C, p);
+}
 
 __global__ void __launch_bounds__(1024) k_scan_P(Colony C) { scan_P_body(C); }
 
@@ -361,7 +396,7 @@ __global__ void k_tour_length(const int2* xy, const int32_t* route, int n, unsig
 }  // namespace
 
 cudaError_t launch_rows(const Colony& C, int update, cudaStream_t s) {
-  k_rows<<<(C.n + 255) / 256, 256, 0, s>>>(C, update);
+  k_rows<<<(unsigned)(((int64_t)C.n * C.kw + 255) / 256), 256, 0, s>>>(C, update);
   return cudaGetLastError();
 }
 
