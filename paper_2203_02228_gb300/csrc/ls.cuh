@@ -61,6 +61,11 @@ struct ArrTour {
   int stride;
   const int32_t* cd;    // their EUC_2D costs, same layout
   __device__ __forceinline__ int pos_of(int x) const { return pos[x]; }
+  // x moves from position `from` to `to`
+  __device__ __forceinline__ void move_pos(int x, int from, int to) {
+    (void)from;
+    pos[x] = to;
+  }
   __device__ __forceinline__ int at_off(int p, int d) const {
     p += d;
     if (p >= n) p -= n;

@@ -108,12 +108,90 @@ struct SpanLog {
   int count;
 };
 
+// The initial search's tour with its positions in shared memory (n up to
+// about 106k nodes fits): the low 16 bits of each position in lo[n], bit 16
+// in the bitmap hi.  Otherwise the same lookups as ArrTour.
+struct SmemPosTour {
+  int n, k;
+  int32_t* route;
+  uint16_t* lo;
+  uint32_t* hi;
+  const int2* xy;
+  const int32_t* cn;
+  const int32_t* cd;
+  __device__ __forceinline__ int pos_of(int x) const {
+    return (int)lo[x] | (int)(((hi[x >> 5] >> (x & 31)) & 1u) << 16);
+  }
+  // x moves from position `from` to `to`; each node moves by one thread at a
+  // time, but the 32 nodes of a bitmap word may move together
+  __device__ __forceinline__ void move_pos(int x, int from, int to) {
+    lo[x] = (uint16_t)to;
+    if ((from ^ to) >> 16) atomicXor(&hi[x >> 5], 1u << (x & 31));
+  }
+  __device__ __forceinline__ int at_off(int p, int d) const {
+    p += d;
+    if (p >= n) p -= n;
+    if (p < 0) p += n;
+    return route[p];
+  }
+  __device__ __forceinline__ int succ(int x) const { return at_off(pos_of(x), 1); }
+  __device__ __forceinline__ int adj(int x, bool up) const { return at_off(pos_of(x), up ? 1 : -1); }
+  __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
+    const int t = pos_of(x);
+    p = at_off(t, -1);
+    s = at_off(t, 1);
+  }
+  __device__ __forceinline__ void walk(int a, int& p, int& s1, int& s2, int& s3) const {
+    const int t = pos_of(a);
+    p = at_off(t, -1);
+    s1 = at_off(t, 1);
+    s2 = at_off(t, 2);
+    s3 = at_off(t, 3);
+  }
+  __device__ __forceinline__ int2 coord(int x) const { return xy[x]; }
+  __device__ __forceinline__ int cand(int x, int s) const { return cn[(size_t)x * k + s]; }
+  __device__ __forceinline__ int cdist(int x, int s) const { return cd[(size_t)x * k + s]; }
+};
+
+// Shared-memory bytes of an n-node SmemPosTour.
+__host__ __device__ __forceinline__ size_t smem_pos_bytes(int n) {
+  return (((size_t)n * 2 + 15) & ~(size_t)15) + (size_t)((n + 31) >> 5) * 4;
+}
+
+__device__ __forceinline__ SmemPosTour smem_pos_tour(unsigned char* sm, int n, int k, int32_t* route,
+                                                     const int2* xy, const int32_t* cand, const int32_t* dcand) {
+  SmemPosTour T;
+  T.n = n;
+  T.k = k;
+  T.route = route;
+  T.lo = reinterpret_cast<uint16_t*>(sm);
+  T.hi = reinterpret_cast<uint32_t*>(sm + (((size_t)n * 2 + 15) & ~(size_t)15));
+  T.xy = xy;
+  T.cn = cand;
+  T.cd = dcand;
+  return T;
+}
+
+// Positions of the tour `route` into T (block).
+__device__ __forceinline__ void smem_pos_load(SmemPosTour& T) {
+  const int n = T.n;
+  for (int w = threadIdx.x; w < ((n + 31) >> 5); w += blockDim.x) T.hi[w] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int x = T.route[i];
+    T.lo[x] = (uint16_t)i;
+    if (i >> 16) atomicOr(&T.hi[x >> 5], 1u << (x & 31));
+  }
+  __syncthreads();
+}
+
 // Reverse the forward span x..y (or its complement) with the whole block;
 // the span actually reversed goes to the log.
-__device__ void cta_flip(ArrTour& T, int x, int y, SpanLog& log) {
+template <class TT>
+__device__ void cta_flip(TT& T, int x, int y, SpanLog& log) {
   const int n = T.n;
   __syncthreads();
-  int i = T.pos[x], j = T.pos[y];
+  int i = T.pos_of(x), j = T.pos_of(y);
   __syncthreads();  // every thread has read i, j before any position moves
   int L = j - i;
   if (L < 0) L += n;
@@ -135,13 +213,14 @@ __device__ void cta_flip(ArrTour& T, int x, int y, SpanLog& log) {
     const int va = T.route[ia], vb = T.route[ib];
     T.route[ia] = vb;
     T.route[ib] = va;
-    T.pos[vb] = ia;
-    T.pos[va] = ib;
+    T.move_pos(vb, ib, ia);
+    T.move_pos(va, ia, ib);
   }
   __syncthreads();
 }
 
-__device__ void cta_move2(ArrTour& T, int n1, int n2, int n3, int n4, SpanLog& log) {
+template <class TT>
+__device__ void cta_move2(TT& T, int n1, int n2, int n3, int n4, SpanLog& log) {
   const bool fwd = T.succ(n1) == n2;
   if (fwd)
     cta_flip(T, n2, n3, log);
@@ -171,17 +250,18 @@ __device__ __forceinline__ bool in_span(int p, int2 sp, int n) {
 // popping one node at a time.
 constexpr int kWin = 32;
 
-__device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_t* cand, const int32_t* dcand,
-                                             int k, int oropt, int verify, int32_t* route, int32_t* pos,
-                                             int32_t* queue, uint8_t* flags, int32_t* logb) {
+template <class TT>
+__device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32_t* queue, uint8_t* flags,
+                                             int32_t* logb) {
   __shared__ int64_t s_gain[kWin];
   __shared__ int s_mv[kWin][8];
   __shared__ int s_node[kWin];            // node whose evaluation the slot holds, -1: none
   __shared__ int s_dep[kWin][kMaxK + 1];  // [0]: its position, [1 + s]: candidate s's position
   __shared__ SpanLog s_log;
   __shared__ int s_qh, s_qn, s_nlog, s_changes, s_moves_round, s_win, s_base;
+  const int n = T.n, k = T.k;
+  int32_t* route = T.route;
   LsEnv E{n, oropt, verify, queue, flags, logb};
-  ArrTour T{n, k, route, pos, xy, cand, k, dcand};
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   for (int i = tid; i < n; i += blockDim.x) {
     const int x = route[i];
@@ -236,9 +316,9 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
         int mv2[4], mvo[7];
         int64_t g2, go;
         eval_both(T, my_node, oropt != 0, g2, mv2, go, mvo);
-        if (lane < k) s_dep[my_slot][1 + lane] = T.pos[T.cand(my_node, lane)];
+        if (lane < k) s_dep[my_slot][1 + lane] = T.pos_of(T.cand(my_node, lane));
         if (lane == 0) {
-          s_dep[my_slot][0] = T.pos[my_node];
+          s_dep[my_slot][0] = T.pos_of(my_node);
           if (g2 > 0) {
             s_gain[my_slot] = g2;
             for (int t = 0; t < 4; ++t) s_mv[my_slot][t] = mv2[t];
@@ -343,19 +423,52 @@ __device__ __forceinline__ void init_ls_body(const int2* xy, int n, const int32_
   for (int i = tid; i < nl; i += blockDim.x) flags[logb[i]] = 0;
 }
 
+// SP: the positions live in shared memory during the search (launched with
+// smem_pos_bytes(n) of it) and are written to `pos` at the end; otherwise
+// the search works on `pos` in global memory.
+template <bool SP>
+__device__ __forceinline__ void init_ls_run(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k,
+                                            int oropt, int verify, int32_t* route, int32_t* pos, int32_t* queue,
+                                            uint8_t* flags, int32_t* logb) {
+  if constexpr (SP) {
+    extern __shared__ __align__(16) unsigned char s_pos[];
+    SmemPosTour T = smem_pos_tour(s_pos, n, k, route, xy, cand, dcand);
+    smem_pos_load(T);
+    init_ls_body(T, oropt, verify, queue, flags, logb);
+    __syncthreads();
+    for (int x = threadIdx.x; x < n; x += blockDim.x) pos[x] = T.pos_of(x);
+  } else {
+    ArrTour T{n, k, route, pos, xy, cand, k, dcand};
+    init_ls_body(T, oropt, verify, queue, flags, logb);
+  }
+}
+
+template <bool SP>
 __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand,
                                                   const int32_t* dcand, int k, int oropt, int verify,
                                                   int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                                                   int32_t* logb) {
-  init_ls_body(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+  init_ls_run<SP>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
 }
 
 // Batch: one block per colony; positions of the initial tour in src_pos.
+template <bool SP>
 __global__ void __launch_bounds__(1024) k_init_ls_b(const Colony* cols, const ColonySetup* sets) {
   const Colony C = cols[blockIdx.x];
   const ColonySetup S = sets[blockIdx.x];
-  init_ls_body(C.xy, C.n, S.cand, S.dcand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags,
-               S.logb);
+  init_ls_run<SP>(C.xy, C.n, S.cand, S.dcand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags,
+                  S.logb);
+}
+
+// Shared memory for positions of up to n nodes if kernel f can take it,
+// else 0 (the positions then stay in global memory).
+size_t init_ls_pos_smem(const void* f, int n) {
+  const size_t b = smem_pos_bytes(n);
+  if (allow_dyn_smem(f, b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return b;
 }
 
 // what = 0: Philox draws   in: uint32 [count][4] = (idx, ant, iter, tag) -> out uint32
@@ -403,7 +516,11 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
                            int verify, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s) {
-  k_init_ls<<<1, 1024, 0, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+  const size_t sm = init_ls_pos_smem(reinterpret_cast<const void*>(k_init_ls<true>), n);
+  if (sm > 0)
+    k_init_ls<true><<<1, 1024, sm, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+  else
+    k_init_ls<false><<<1, 1024, 0, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
   return cudaGetLastError();
 }
 
@@ -417,7 +534,11 @@ cudaError_t launch_init_tour_batch(const Colony* cols, const ColonySetup* sets, 
     }
     k_nn_tour_b<<<count, 32, smem, s>>>(cols, sets);
   } else {
-    k_init_ls_b<<<count, 1024, 0, s>>>(cols, sets);
+    const size_t sm = init_ls_pos_smem(reinterpret_cast<const void*>(k_init_ls_b<true>), max_n);
+    if (sm > 0)
+      k_init_ls_b<true><<<count, 1024, sm, s>>>(cols, sets);
+    else
+      k_init_ls_b<false><<<count, 1024, 0, s>>>(cols, sets);
   }
   return cudaGetLastError();
 }

@@ -154,3 +154,23 @@ def test_batch_base_faco():
             assert lens[i] == L, (plan, i)
             np.testing.assert_array_equal(tours[i], t)
             assert same_bits(b.tau(i), c.tau())
+
+
+def test_initial_search_with_positions_in_global_memory():
+    """A batch whose largest colony is too large for the initial search's
+    shared-memory positions runs every colony's initial search on positions
+    in global memory; the small colonies must still equal their one-colony
+    runs, which keep the positions in shared memory."""
+    xs = [inputs.uniform(120_000, seed=71), inputs.uniform(900, seed=72), inputs.stippled(2000, seed=73, blobs=4,
+                                                                                           ridges=1, side=60_000)]
+    seeds = np.array([5, 6, 7], dtype=np.uint64)
+    b = Batch(xs, 16, seeds=seeds)
+    b.iterate(8, 1)
+    tours, lens = b.tours()
+    for i in (1, 2):
+        c = Colony(xs[i], 16, seed=int(seeds[i]))
+        c.iterate(8, 1)
+        t, L = c.best()
+        assert lens[i] == L, i
+        np.testing.assert_array_equal(tours[i], t)
+        assert b.stats(i).initial_length == c.stats().initial_length
