@@ -571,7 +571,7 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
 // memory: warp 0 constructs, then all warps run the local search with
 // speculative in-order pops (ls_run_block).  An ant whose table fills up is
 // marked and redone by the array kernel.
-constexpr int kAntWarps = 4;
+constexpr int kAntWarps = 5;
 
 __device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
   A.stats[(size_t)ant * kNStats + kStRedo] += 1;
