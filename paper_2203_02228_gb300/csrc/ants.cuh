@@ -570,8 +570,13 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
 // One block of kAntWarps warps per ant, tour as a segment table in shared
 // memory: warp 0 constructs, then all warps run the local search with
 // speculative in-order pops (ls_run_block).  An ant whose table fills up is
-// marked and redone by the array kernel.
-constexpr int kAntWarps = 5;
+// marked and redone by the array kernel.  All ants of a launch should be
+// resident at once (it lasts as long as its slowest ant), so seven blocks
+// per SM; each thread then gets the largest multiple of 8 registers that
+// fits seven blocks in the register file.
+constexpr int kAntWarps = 6;
+constexpr int kAntBlocksPerSM = 7;
+constexpr int kAntMaxRegs = (65536 / (kAntBlocksPerSM * 32 * kAntWarps)) & ~7;
 
 __device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
   A.stats[(size_t)ant * kNStats + kStRedo] += 1;
@@ -595,7 +600,7 @@ __global__ void __launch_bounds__(128, 1) k_ants(Colony C, Ants A) {
 }
 
 template <int KW>
-__global__ void __launch_bounds__(32 * kAntWarps, 7) k_ants_blk(Colony C, Ants A) {
+__global__ void __maxnreg__(kAntMaxRegs) k_ants_blk(Colony C, Ants A) {
   const int ant = blockIdx.x;
   if (ant >= A.m) return;
 #define ANTS_BLK_OVERFLOW (void)0
@@ -613,7 +618,7 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, size_t by
 // Batch: block b runs ant map[b].y of colony map[b].x; an ant whose table
 // filled up is appended to the redo list.
 template <int KW>
-__global__ void __launch_bounds__(32 * kAntWarps, 7)
+__global__ void __maxnreg__(kAntMaxRegs)
     k_ants_blk_b(const Colony* cols, const Ants* ants, const int2* map, int2* redo_list, int32_t* redo_n) {
   __shared__ Colony sC;
   __shared__ Ants sA;
