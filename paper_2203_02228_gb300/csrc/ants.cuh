@@ -570,13 +570,13 @@ __device__ __forceinline__ void ants_arr_body(const Colony& C, const Ants& A, in
 // One block of kAntWarps warps per ant, tour as a segment table in shared
 // memory: warp 0 constructs, then all warps run the local search with
 // speculative in-order pops (ls_run_block).  An ant whose table fills up is
-// marked and redone by the array kernel.  All ants of a launch should be
-// resident at once (it lasts as long as its slowest ant), so seven blocks
-// per SM; each thread then gets the largest multiple of 8 registers that
-// fits seven blocks in the register file.
-constexpr int kAntWarps = 6;
-constexpr int kAntBlocksPerSM = 7;
-constexpr int kAntMaxRegs = (65536 / (kAntBlocksPerSM * 32 * kAntWarps)) & ~7;
+// marked and redone by the array kernel.  A launch lasts as long as its
+// slowest ant; wider blocks speculate deeper, so the slowest ants finish
+// sooner, while fewer blocks fit an SM (with 64 registers, four blocks of
+// eight warps: 608 of 1,024 ants start at once, the rest as the quick ones
+// finish).  Measured best of 4..12 warps and 40..72 registers.
+constexpr int kAntWarps = 8;
+constexpr int kAntMaxRegs = 64;
 
 __device__ __forceinline__ void st_redo_add(const Ants& A, int ant) {
   A.stats[(size_t)ant * kNStats + kStRedo] += 1;

@@ -451,7 +451,7 @@ int Runner::kernels_per_iteration() const {
 // ---------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune;  // (device, class, m, kw, k) -> variant
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;  // (device, class, m, kw, goal) -> variant
 
 int cur_device() {
   int d = 0;
@@ -466,25 +466,25 @@ int size_class(int n) {
   return c;  // [3, 512), [512, 2048), [2048, 8192), ...
 }
 
-int tuner_get(int cls, int m, int kw) {
+int tuner_get(int cls, int m, int kw, int goal) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tune.find(std::make_tuple(cur_device(), cls, m, kw, 0));
+  auto it = g_tune.find(std::make_tuple(cur_device(), cls, m, kw, goal));
   return it == g_tune.end() ? -1 : it->second;
 }
 
-void tuner_put(int cls, int m, int kw, int variant) {
+void tuner_put(int cls, int m, int kw, int variant, int goal) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[std::make_tuple(cur_device(), cls, m, kw, 0)] = variant;
+  g_tune[std::make_tuple(cur_device(), cls, m, kw, goal)] = variant;
 }
 
-int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s) {
+int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s, int goal) {
   // the untuned classes, and up to 64 colonies of each (spread over the
   // class when it has more)
   std::map<std::pair<int, int>, std::vector<RunEntry>> cls;
   for (const RunEntry& e : entries) {
     const int c = size_class(e.g->n[e.i]);
     const int m = e.a->m;
-    if (tuner_get(c, m, e.g->kw) >= 0) continue;
+    if (tuner_get(c, m, e.g->kw, goal) >= 0) continue;
     cls[std::make_pair(c, m)].push_back(e);
   }
   for (auto& kv : cls) {
@@ -537,14 +537,14 @@ int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s)
         const int per_sm = ants_batch_resident(variant, v[0].g->kw,
                                                variant == kVarTable ? r.smem_blk : 4 * r.per_warp);
         const double slots = (double)per_sm * sms;
-        const double frac = slots > 0 ? std::min(1.0, ants / slots) : 1.0;
+        const double frac = goal == kTuneBatch && slots > 0 ? std::min(1.0, ants / slots) : 1.0;
         t[variant] = (float)(tmin * frac);
       }
       if (rc != FACO_OK) break;
       for (int variant = 0; variant < kNVariants; ++variant)
         if (t[variant] < t[best]) best = variant;
     }
-    tuner_put(kv.first.first, kv.first.second, v[0].g->kw, best);
+    tuner_put(kv.first.first, kv.first.second, v[0].g->kw, best, goal);
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);

@@ -110,12 +110,18 @@ struct Runner {
 
 // Size class of an instance for the tuner (factors of 4 in n).
 int size_class(int n);
-// Cached choice for (size class, ants, roulette width) on this device; -1 if none.
-int tuner_get(int cls, int m, int kw);
-void tuner_put(int cls, int m, int kw, int variant);
-// Times both per-ant kernels on the colonies of each untuned size class of
-// `entries` (per-ant buffers only are written) and records the faster.
-int tuner_run(const std::vector<RunEntry>& entries, size_t smem_blk, cudaStream_t s);
+// Tuner objective: a batch's throughput (a size class's time scaled by the
+// share of the GPU's resident ant slots it holds, the rest serving the
+// other classes) or one request's latency (its time alone).
+enum TuneGoal { kTuneBatch = 0, kTuneLatency = 1 };
+// Cached choice for (size class, ants, roulette width, goal) on this
+// device; -1 if none.
+int tuner_get(int cls, int m, int kw, int goal = kTuneBatch);
+void tuner_put(int cls, int m, int kw, int variant, int goal = kTuneBatch);
+// Times every per-ant kernel on the colonies of each untuned size class of
+// `entries` (per-ant buffers only are written) and records the best for
+// the goal.
+int tuner_run(const std::vector<RunEntry>& entries, size_t smem_blk, cudaStream_t s, int goal = kTuneBatch);
 
 size_t batch_smem_blk(int kw);
 

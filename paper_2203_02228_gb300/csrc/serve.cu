@@ -207,18 +207,18 @@ std::vector<RunEntry> entries(const std::vector<Request*>& list) {
 }
 
 // The kernel of a request whose set-up is complete (tuned once per size
-// class and ant count, then cached).
+// class and ant count for the request's own latency, then cached).
 int choose_variant(faco_server* s, Request* r) {
   const int cls = size_class(r->n);
-  int v = tuner_get(cls, r->ants, r->g.kw);
+  int v = tuner_get(cls, r->ants, r->g.kw, kTuneLatency);
   if (v < 0) {
     std::vector<RunEntry> e{RunEntry{&r->g, 0, &r->a, kVarArr8}};
     cudaStream_t st = s->lane[r->cohort];
-    int rc = tuner_run(e, s->smem_blk[wslot(r)], st);
+    int rc = tuner_run(e, s->smem_blk[wslot(r)], st, kTuneLatency);
     if (rc != FACO_OK) return rc;
     rc = antset_zero(r->a, st);  // counters of the trial launches
     if (rc != FACO_OK) return rc;
-    v = tuner_get(cls, r->ants, r->g.kw);
+    v = tuner_get(cls, r->ants, r->g.kw, kTuneLatency);
   }
   if (v < 0 || (v == kVarTable && r->a.cap[0] <= 0)) v = kVarArr8;
   r->variant = v;
