@@ -15,7 +15,7 @@
  *   faco_create_ex(coords_xy[i], ns[i], k, p_i, ...) followed by the same
  *   faco_iterate(ants, budget) calls,
  * where p_i is *p with seed = seeds[i] (or p->seed when seeds is NULL).
- * The kernel choice per colony (a block of six warps per ant on a segment
+ * The kernel choice per colony (a block of eight warps per ant on a segment
  * table in shared memory, or one warp per ant on explicit arrays compiled
  * for 2, 4 or 8 resident blocks of four ants per SM; chosen per size class
  * by a timing autotuner or fixed with faco_batch_set_plan) changes only the

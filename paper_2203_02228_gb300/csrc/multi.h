@@ -77,7 +77,7 @@ struct RunEntry {
   int variant;                  // kVariant*
 };
 
-// Per-ant kernel of a colony: a block of four warps per ant on a segment
+// Per-ant kernel of a colony: a block of eight warps per ant on a segment
 // table, or one warp per ant on explicit arrays with the kernel compiled for
 // 2, 4 or 8 resident blocks per SM.
 enum : int { kVarTable = 0, kVarArr2 = 1, kVarArr4 = 2, kVarArr8 = 3, kNVariants = 4 };
