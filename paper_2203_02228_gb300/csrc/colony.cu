@@ -15,9 +15,28 @@ namespace {
 //   tau' = max(tau_min, min(tau_max, fmaf(rho, tau, delta * [edge in source])))
 //   Wsrc[p][s] = tau' * eta,  Csrc[p][s] = source position of cand[u][s].
 // update = 0 only sets tau = tau_max (Alg 2 set-up).
+// The source node at p and its two source neighbours, and the trail
+// parameters of this update.
+struct RowCtx {
+  int u, pn, pp;
+  float tmax, tmin, delta;
+};
+
+__device__ __forceinline__ RowCtx row_ctx(const Colony& C, int p) {
+  const int n = C.n;
+  RowCtx r;
+  r.u = C.src_route[p];
+  r.pn = C.src_route[p + 1 == n ? 0 : p + 1];
+  r.pp = C.src_route[p == 0 ? n - 1 : p - 1];
+  r.tmax = C.st->tmax;
+  r.tmin = C.st->tmin;
+  r.delta = C.st->delta;
+  return r;
+}
+
 // Entry s of row p (s < kw).
-__device__ __forceinline__ void rows_entry(const Colony& C, int p, int s, int update) {
-  const int n = C.n, k = C.k, kw = C.kw;
+__device__ __forceinline__ void rows_entry(const Colony& C, const RowCtx& r, int p, int s, int update) {
+  const int k = C.k, kw = C.kw;
   const size_t o = (size_t)p * kw + s;
   if (s >= k) {
     C.Wsrc[o] = 0.0f;
@@ -25,20 +44,16 @@ __device__ __forceinline__ void rows_entry(const Colony& C, int p, int s, int up
     C.Dcsrc[o] = 0;
     return;
   }
-  const int u = C.src_route[p];
-  const size_t idx = (size_t)u * k + s;
+  const size_t idx = (size_t)r.u * k + s;
   const int v = C.cand[idx];
   float t;
   if (update) {
-    const int pn = C.src_route[p + 1 == n ? 0 : p + 1];
-    const int pp = C.src_route[p == 0 ? n - 1 : p - 1];
-    const float tmax = C.st->tmax, tmin = C.st->tmin, delta = C.st->delta;
-    const float dep = (v == pn || v == pp) ? delta : 0.0f;
+    const float dep = (v == r.pn || v == r.pp) ? r.delta : 0.0f;
     t = __fmaf_rn(C.rho, C.tau[idx], dep);
-    t = t < tmax ? t : tmax;
-    t = t > tmin ? t : tmin;
+    t = t < r.tmax ? t : r.tmax;
+    t = t > r.tmin ? t : r.tmin;
   } else {
-    t = C.st->tmax;
+    t = r.tmax;
   }
   C.tau[idx] = t;
   C.Wsrc[o] = __fmul_rn(t, C.eta[idx]);
@@ -48,22 +63,21 @@ __device__ __forceinline__ void rows_entry(const Colony& C, int p, int s, int up
 
 // The per-node parts of row p: coordinates, source edge length, and the
 // grid's point record p with the new source positions.
-__device__ __forceinline__ void rows_node(const Colony& C, int p) {
-  const int n = C.n;
-  const int u = C.src_route[p];
-  const int pn = C.src_route[p + 1 == n ? 0 : p + 1];
-  const int2 xu = C.xy[u];
+__device__ __forceinline__ void rows_node(const Colony& C, const RowCtx& r, int p) {
+  const int2 xu = C.xy[r.u];
   C.XYsrc[p] = xu;
-  C.Dsrc[p] = euc2d(xu, C.xy[pn]);
+  C.Dsrc[p] = euc2d(xu, C.xy[r.pn]);
   const int v = C.cell_pts[p];
   const int2 xv = C.xy[v];
   C.cell_src[p] = make_int4(C.src_pos[v], xv.x, xv.y, v);
 }
 
+// All of row p by one thread (the batch kernel).
 __device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
   if (p >= C.n) return;
-  for (int s = 0; s < C.kw; ++s) rows_entry(C, p, s, update);
-  rows_node(C, p);
+  const RowCtx r = row_ctx(C, p);
+  for (int s = 0; s < C.kw; ++s) rows_entry(C, r, p, s, update);
+  rows_node(C, r, p);
 }
 
 // Exclusive prefix sums of the source edge lengths (one block).
@@ -271,8 +285,9 @@ __global__ void k_rows(Colony C, int update) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(t / C.kw), s = (int)(t % C.kw);
   if (p >= C.n) return;
-  rows_entry(C, p, s, update);
-  if (s == 0) rows_node(C, p);
+  const RowCtx r = row_ctx(C, p);
+  rows_entry(C, r, p, s, update);
+  if (s == 0) rows_node(C, r, p);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_P(Colony C) { scan_P_body(C); }
