@@ -72,14 +72,6 @@ __device__ __forceinline__ void rows_node(const Colony& C, const RowCtx& r, int 
   C.cell_src[p] = make_int4(C.src_pos[v], xv.x, xv.y, v);
 }
 
-// All of row p by one thread (the batch kernel).
-__device__ __forceinline__ void rows_body(const Colony& C, int p, int update) {
-  if (p >= C.n) return;
-  const RowCtx r = row_ctx(C, p);
-  for (int s = 0; s < C.kw; ++s) rows_entry(C, r, p, s, update);
-  rows_node(C, r, p);
-}
-
 // Exclusive prefix sums of the source edge lengths (one block).
 __device__ __forceinline__ void scan_P_body(const Colony& C) {
   // tiles of 8 consecutive edges per thread, read and written coalesced,
@@ -302,10 +294,22 @@ __global__ void k_state_init(Colony C, const int64_t* len) {
   if (threadIdx.x == 0 && blockIdx.x == 0) state_init_body(C, len);
 }
 
+// Block e.y of colony e.x covers the rows of nodes e.y * blockDim.x onward
+// (as many as threads); its threads take the row entries in order, so that
+// consecutive threads write consecutive entries.
 __global__ void k_rows_b(const Colony* cols, const int2* map, int update) {
   const int2 e = map[blockIdx.x];
   const Colony C = cols[e.x];
-  rows_body(C, e.y * blockDim.x + threadIdx.x, update);
+  const int p0 = e.y * blockDim.x;
+  const int rows = min((int)blockDim.x, C.n - p0);
+  if (rows <= 0) return;
+  const int kw = C.kw;
+  for (int q = threadIdx.x; q < rows * kw; q += blockDim.x) {
+    const int p = p0 + q / kw, s = q % kw;
+    const RowCtx r = row_ctx(C, p);
+    rows_entry(C, r, p, s, update);
+    if (s == 0) rows_node(C, r, p);
+  }
 }
 
 __global__ void __launch_bounds__(1024) k_scan_P_b(const Colony* cols) {
