@@ -186,11 +186,11 @@ __device__ __forceinline__ void smem_pos_load(SmemPosTour& T) {
 }
 
 // Reverse the forward span x..y (or its complement) with the whole block;
-// the span actually reversed goes to the log.
+// the span actually reversed goes to the log.  Every caller reaches it
+// after a block barrier that follows the last write to the tour.
 template <class TT>
 __device__ void cta_flip(TT& T, int x, int y, SpanLog& log) {
   const int n = T.n;
-  __syncthreads();
   int i = T.pos_of(x), j = T.pos_of(y);
   __syncthreads();  // every thread has read i, j before any position moves
   int L = j - i;
@@ -364,7 +364,9 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
     if (win >= 0) {
       int mv[8];
       for (int t = 0; t < 8; ++t) mv[t] = s_mv[win][t];
-      __syncthreads();  // every thread has the move before its slot is freed
+      // the slot is free (its move is not overwritten before the next
+      // evaluation phase, several barriers on); the warp checking it below
+      // may still read the old node, which leaves the slot free either way
       if (tid == 0) s_node[win] = -1;
       if (mv[7] == 0) {
         cta_flip(T, mv[1], mv[2], s_log);
