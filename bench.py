@@ -55,6 +55,26 @@ METRIC = "ant-solutions/sec at 100k nodes"
 UNIT = "ant-solutions/s"
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values, on every rank (x itself on one
+    rank).  `device` holds the reduced tensor: the GPU under NCCL, "cpu"
+    under gloo."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units of every rank over the slowest
+    rank's time (ms)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -494,12 +514,8 @@ def main():
     barrier()
     clk = clocks.stop()
 
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ants * iters * world / (ms / 1e3)
+    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
+    value = job_throughput(ants * iters, world, ms)
 
     # end to end through the host API (pinned host coordinates, host tour)
     e2e = None
@@ -520,12 +536,8 @@ def main():
             t1 = time.perf_counter()
             faco_destroy(h)
             e2e_ms.append((t1 - t0) * 1e3)
-        em = statistics.mean(e2e_ms)
-        if world > 1:
-            t = torch.tensor([em], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            em = float(t.item())
-        e2e = {"value": ants * iters * world / (em / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+        em = max_over_ranks(statistics.mean(e2e_ms), world, dev)
+        e2e = {"value": job_throughput(ants * iters, world, em), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": 4 * n + 8, "ms_per_step": em}
 
     peak, peak_src = load_peaks()
