@@ -91,6 +91,16 @@ int faco_server_release(faco_server* s, uint64_t ticket);
 
 int faco_server_stats_get(faco_server* s, faco_server_stats* st);
 
+/* Test hook (host only; needs no GPU): replays a script of `count`
+ * operations on a pool of `pool_bytes` (at most 2^26) with the server's
+ * allocator -- first fit in 256-byte granules, freed ranges merged with
+ * free neighbours.  ops[2i] > 0: take that many bytes; ops[2i] == 0: give
+ * back the range taken by operation ops[2i+1] (an earlier, still held
+ * take).  out[2i] = the offset taken (-1: no room; 0 for a give-back),
+ * out[2i+1] = bytes in use after the operation.  FACO_E_ARG on a malformed
+ * script. */
+int faco_test_pool(int64_t pool_bytes, const int64_t* ops, int32_t count, int64_t* out);
+
 /* Drops the requests still waiting for memory (their status becomes
  * FACO_E_STATE), lets the admitted ones run to the end of their budgets,
  * stops the scheduler and frees everything; results are then gone. */

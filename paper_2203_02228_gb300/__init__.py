@@ -395,3 +395,13 @@ def device_selftest(what: int, inp: np.ndarray, out: np.ndarray, count: int, wid
     """Runs a device primitive through the library (see faco_test_device)."""
     _lib.check(load().faco_test_device(what, _ptr(inp), inp.nbytes, _ptr(out), out.nbytes, count, width, seed),
                "faco_test_device")
+
+
+def pool_replay(pool_bytes: int, ops: np.ndarray) -> np.ndarray:
+    """Replays take / give-back operations on the server's device-memory
+    allocator, on the host (see faco_test_pool).  ops: int64 [count][2];
+    returns int64 [count][2] (offset taken or -1, bytes in use after)."""
+    ops = np.ascontiguousarray(ops, dtype=np.int64)
+    out = np.zeros_like(ops)
+    _lib.check(load().faco_test_pool(int(pool_bytes), _ptr(ops), int(ops.shape[0]), _ptr(out)), "faco_test_pool")
+    return out

@@ -147,6 +147,7 @@ def load():
             "faco_server_release": (ctypes.c_int, [vp, ctypes.c_uint64]),
             "faco_server_stats_get": (ctypes.c_int, [vp, P(faco_server_stats)]),
             "faco_server_destroy": (None, [vp]),
+            "faco_test_pool": (ctypes.c_int, [i64, vp, i32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

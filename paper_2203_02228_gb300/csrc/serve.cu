@@ -544,6 +544,33 @@ int faco_server_stats_get(faco_server* s, faco_server_stats* st) {
   return FACO_OK;
 }
 
+int faco_test_pool(int64_t pool_bytes, const int64_t* ops, int32_t count, int64_t* out) {
+  if (pool_bytes < 0 || pool_bytes > ((int64_t)1 << 26) || count < 0 || (count > 0 && (!ops || !out)))
+    return FACO_E_ARG;
+  std::vector<char> mem((size_t)pool_bytes + 1);
+  Pool pool;
+  pool.init(mem.data(), (size_t)pool_bytes);
+  std::vector<char*> got((size_t)count, nullptr);
+  std::vector<size_t> got_bytes((size_t)count, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t a = ops[2 * (size_t)i], b = ops[2 * (size_t)i + 1];
+    if (a > 0) {
+      char* p = pool.get((size_t)a);
+      got[i] = p;
+      got_bytes[i] = (size_t)a;
+      out[2 * (size_t)i] = p ? (int64_t)(p - mem.data()) : -1;
+    } else if (a == 0 && b >= 0 && b < i && got[b]) {
+      pool.put(got[b], got_bytes[b]);
+      got[b] = nullptr;
+      out[2 * (size_t)i] = 0;
+    } else {
+      return FACO_E_ARG;
+    }
+    out[2 * (size_t)i + 1] = (int64_t)pool.in_use();
+  }
+  return FACO_OK;
+}
+
 void faco_server_destroy(faco_server* s) {
   if (!s) return;
   {
