@@ -124,7 +124,6 @@ def test_roulette_edge_cases():
             continue
         s = oracle.roulette(w, float(np.nextafter(np.float32(1), np.float32(0))))
         assert w[s] > 0
-        assert s == int(np.nonzero(w > 0)[0][-1]) or True
 
 
 def test_roulette_zero_padding_to_32_is_equivalent():

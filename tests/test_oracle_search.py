@@ -317,3 +317,84 @@ def test_base_faco_keeps_constructed_tours():
     bt, bl = base.ant_tours()
     pt, pl, _ = base.ant_pre()
     np.testing.assert_array_equal(bt, pt)
+
+
+# ---- trail limits (Sec. 4.5) and the source choice (Sec. 5.2) ---------------
+
+@pytest.mark.parametrize("n,k", [(40, 16), (300, 16), (300, 8), (1000, 5), (2500, 32), (700, 2)])
+def test_tau_min_meets_its_defining_probability(n, k):
+    """Sec. 4.5: tau_min is set so that, once the trails have converged (one
+    edge at tau_max among `avg` choices, the rest at tau_min), an ant picking
+    by pheromone alone takes the tau_max edge at each of its n decisions with
+    probability p_dec = tau_max / (tau_max + (avg - 1) tau_min), and builds
+    the best solution with probability p_dec^n = p_best.  FACO with local
+    search takes avg = cl_size (the candidate list length k).  The check is
+    the derivation's property, not the closed form: a wrong avg (the MMAS
+    n/2), a dropped n-th root or a swapped (avg - 1) gives another p_dec^n."""
+    xy = inputs.uniform(n, seed=500 + n + k)
+    for p_best in (0.05, 0.5):
+        C = oracle.Colony(xy, k, p_best=p_best)
+        tmax, tmin, tmax32, tmin32 = C.limits()
+        kk = min(k, n - 1)
+        p_dec = tmax / (tmax + (kk - 1) * tmin)
+        # p_dec^n = exp(n log p_dec): relative error ~ n * 1e-16 from rounding
+        assert abs(math.exp(n * math.log(p_dec)) / p_best - 1.0) < 1e-11 * n
+        # the same colony with another p_best moves tau_min the right way
+        assert tmin32 == np.float32(tmin) and tmax32 == np.float32(tmax)
+    lo = oracle.Colony(xy, k, p_best=0.01).limits()[1]
+    hi = oracle.Colony(xy, k, p_best=0.5).limits()[1]
+    assert hi < lo  # a larger p_best means a sharper contrast, a smaller tau_min
+
+
+def _source_run(xy, p_src, iters, seed=3, ants=3):
+    C = oracle.Colony(xy, 16, seed=seed, p_source_gb=p_src, threads=2)
+    rows = []
+    for it in range(1, iters + 1):
+        hist, alh = C.iterate(ants, 1)
+        tours, lens = C.ant_tours()
+        src, src_len = C.source()
+        best, best_len = C.best()
+        rows.append((it, hist[0], alh[0], tours, lens, src, src_len, best, best_len))
+    return rows
+
+
+@pytest.mark.parametrize("p_src", [0.01, 0.3])
+def test_source_is_global_best_with_probability_p(p_src):
+    """Alg 2 ("choose between global_best and iter_best"), Sec. 5.2: after
+    each iteration the source is the best-so-far tour with probability
+    p_source_gb, else the iteration's best tour (shortest, lowest ant index
+    on ties).  Checked iteration by iteration against the tours themselves,
+    and the share of global-best sources against a binomial bound; an
+    inverted draw (global best with probability 1 - p) fails both."""
+    xy = inputs.uniform(30, seed=91, side=3000)
+    iters = 600
+    rows = _source_run(xy, p_src, iters)
+    used_gb = 0
+    for it, h, alh, tours, lens, src, src_len, best, best_len in rows:
+        ib = int(np.argmin(lens))  # first index of the minimum
+        assert h[0] == lens[ib] and h[1] == ib and h[2] == best_len
+        np.testing.assert_array_equal(alh, lens)
+        if h[3]:
+            used_gb += 1
+            np.testing.assert_array_equal(src, best)
+            assert src_len == best_len
+        else:
+            np.testing.assert_array_equal(src, tours[ib])
+            assert src_len == lens[ib]
+        # the decision is the colony's Philox draw (tag 1, draw 0) of this
+        # iteration; the generator itself is pinned by known-answer vectors
+        assert bool(h[3]) == (oracle.u01(oracle.draw(3, 0, 0, it, 1)) < p_src)
+    mean, sd = iters * p_src, math.sqrt(iters * p_src * (1 - p_src))
+    assert abs(used_gb - mean) <= 5 * sd + 1
+    # the two arms must both occur for the check above to mean anything
+    assert 0 < used_gb < iters
+
+
+@pytest.mark.parametrize("p_src,want", [(0.0, 0), (1.0, 1)])
+def test_source_choice_extremes(p_src, want):
+    """p_source_gb = 0: always the iteration best; = 1: always the best so
+    far (u01 < 1 always holds)."""
+    rows = _source_run(inputs.uniform(25, seed=92, side=3000), p_src, 40)
+    for it, h, alh, tours, lens, src, src_len, best, best_len in rows:
+        assert h[3] == want
+        np.testing.assert_array_equal(src, best if want else tours[int(np.argmin(lens))])
