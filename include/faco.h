@@ -220,6 +220,16 @@ int faco_get_ant_stats(faco_ctx* c, int64_t* stats);
 int faco_lists_noalloc(const int32_t* coords_dev, int32_t n, int32_t k, int32_t bl, int32_t* cand_dev,
                        int32_t* backup_dev, float* eta_dev, void* stream);
 
+/* ---- L2 bandwidth probe (diagnostics) --------------------------------------
+ * The paper has no counterpart.  Measures the L2 read bandwidth of the
+ * current device: a buffer of `bytes` (1 MiB .. 1 GiB; pick one well inside
+ * the L2, e.g. 48 MiB) is filled, read once to bring it into L2, then read
+ * `reps` times (1..100000) by 4 blocks per SM with 16-byte L1-bypassing
+ * loads; *gbs = bytes * reps / the timed kernel's CUDA-event duration, in
+ * GB/s.  Allocates and frees its own device buffers and stream; synchronous.
+ * Errors: FACO_E_ARG, FACO_E_NOMEM, FACO_E_CUDA. */
+int faco_l2_probe(size_t bytes, int32_t reps, double* gbs);
+
 /* ---- device self-test hook (used by the test-suite) ----------------------
  * Runs one of the library's device primitives on `count` inputs copied from
  * host memory and copies the results back (synchronous, default stream):

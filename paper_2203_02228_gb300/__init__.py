@@ -391,6 +391,13 @@ class Server:
         return {f: getattr(st, f) for f, _ in st._fields_}
 
 
+def l2_probe(bytes_: int = 48 << 20, reps: int = 200) -> float:
+    """L2 read bandwidth of the current device in GB/s (see faco_l2_probe)."""
+    g = ctypes.c_double()
+    _lib.check(load().faco_l2_probe(int(bytes_), int(reps), ctypes.byref(g)), "faco_l2_probe")
+    return float(g.value)
+
+
 def device_selftest(what: int, inp: np.ndarray, out: np.ndarray, count: int, width: int = 16, seed: int = 0) -> None:
     """Runs a device primitive through the library (see faco_test_device)."""
     _lib.check(load().faco_test_device(what, _ptr(inp), inp.nbytes, _ptr(out), out.nbytes, count, width, seed),

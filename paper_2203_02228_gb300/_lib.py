@@ -124,6 +124,7 @@ def load():
             "faco_lists_noalloc": (ctypes.c_int, [vp, i32, i32, i32, vp, vp, vp, vp]),
             "faco_profile_enable":(ctypes.c_int, [vp, ctypes.c_int]),
             "faco_profile_read": (ctypes.c_int, [vp, P(ctypes.c_double), P(i64)]),
+            "faco_l2_probe": (ctypes.c_int, [ctypes.c_size_t, i32, P(ctypes.c_double)]),
             "faco_test_device":(ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_size_t,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
             # include/faco_batch.h

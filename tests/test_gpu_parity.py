@@ -229,3 +229,53 @@ def test_uniform1k_full_workload_bit_exact():
     oh, oal = o.iterate(32, 200)
     np.testing.assert_array_equal(g.history(), oh)
     assert_same_state(g, o, 32)
+
+
+def test_stippled200k_setup_and_first_iterations():
+    """The n = 200,000 stippled workload (256 blobs) at full size in the
+    benchmark's launch configuration (2,048 ants): lists, initial tour
+    (its local search keeps positions in global memory at this size),
+    limits, and the first two iterations -- every ant's length, a sample
+    of tours, the history and tau bits."""
+    xy = inputs.workload_points("stippled200k")
+    g = Colony(xy, 16, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, threads=16)
+    gc, gb, ge = g.lists()
+    oc, ob, oe = o.lists()
+    np.testing.assert_array_equal(gc, oc)
+    np.testing.assert_array_equal(gb, ob)
+    assert np.array_equal(ge.view(np.uint32), oe.view(np.uint32))
+    assert g.initial()[1] == o.initial()[1]
+    np.testing.assert_array_equal(g.initial()[0], o.initial()[0])
+    np.testing.assert_array_equal(g.limits(), o.limits())
+    o_hist = []
+    for it in range(2):
+        g.iterate(2048, 1)
+        oh, oal = o.iterate(2048, 1)
+        o_hist.append(oh[0])
+        gt, gl = g.ant_tours()
+        np.testing.assert_array_equal(gl, oal[0], err_msg="iteration %d" % (it + 1))
+        ot, _ = o.ant_tours()
+        sample = np.arange(3, 2048, 131)
+        np.testing.assert_array_equal(gt[sample], ot[sample])
+        del gt, ot
+    np.testing.assert_array_equal(g.history(), np.array(o_hist))
+    assert_same_state(g, o, 2048)
+    assert g.stats().redone_ants >= 0
+
+
+def test_one_colony_above_shared_position_limit():
+    """n = 120,000 (stippled): the initial local search of a single colony
+    keeps tour positions in global memory above ~106k nodes; its lists,
+    initial tour and one iteration of 256 ants against the oracle."""
+    xy = inputs.stippled(120_000, seed=1212, blobs=48, ridges=6, side=100_000)
+    g = Colony(xy, 16, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, threads=16)
+    np.testing.assert_array_equal(g.lists()[0], o.lists()[0])
+    assert g.initial()[1] == o.initial()[1]
+    np.testing.assert_array_equal(g.initial()[0], o.initial()[0])
+    g.iterate(256, 1)
+    oh, oal = o.iterate(256, 1)
+    np.testing.assert_array_equal(g.ant_tours()[1], oal[0])
+    np.testing.assert_array_equal(g.history()[-1], oh[0])
+    assert_same_state(g, o, 256)
