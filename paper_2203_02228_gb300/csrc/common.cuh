@@ -201,9 +201,37 @@ __device__ __forceinline__ int32_t euc2d_m(uint64_t m) {
   return (int32_t)(r + ((m - rr) > r ? 1u : 0u));
 }
 
+// The same cost of two points, on a short dependency chain.  An FP32
+// estimate d of sqrt(dx^2 + dy^2) is accepted when the exact integer test
+// d^2 - d < m <= d^2 + d holds, which says (d - 1/2)^2 < m < (d + 1/2)^2,
+// i.e. d = nint(sqrt(m)); otherwise the exact integer steps of euc2d_m
+// decide.  The estimate: |dx|, |dy| < 2^22 convert to FP32 exactly by the
+// 1.5 * 2^23 bias (an add on the bit pattern and a float subtract), the
+// hardware's approximate square root (sqrt.approx.f32) follows, and an
+// estimate below 2^22 rounds to the nearest integer by the same bias.  Its
+// relative error is about 2^-21, so the test fails only for costs above
+// ~10^6, next to a half-integer, or with |dx| or |dy| >= 2^22 (where the
+// bias tricks do not hold and the estimate is meaningless): those, and
+// m = 0 (d = 0 fails the test), take the exact path.
+__device__ __forceinline__ float i2f_biased(int32_t v) {  // exact for |v| < 2^22
+  return __fsub_rn(__int_as_float(v + 0x4B400000), 12582912.0f);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ int32_t euc2d(int2 a, int2 b) {
   const int32_t dx = a.x - b.x, dy = a.y - b.y;  // |dx|, |dy| < 2^24
-  return euc2d_m((uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy));
+  const uint64_t m = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy);
+  const float fx = i2f_biased(dx), fy = i2f_biased(dy);
+  const float mf = __fmaf_rn(fx, fx, __fmul_rn(fy, fy));
+  const uint32_t d = (uint32_t)(__float_as_int(__fadd_rn(sqrt_approx(mf), 12582912.0f)) - 0x4B400000);
+  const uint64_t dd = (uint64_t)d * d;
+  if (m > dd - d && m <= dd + d) return (int32_t)d;
+  return euc2d_m(m);
 }
 
 // ---------------------------------------------------------------------

@@ -55,10 +55,26 @@ def test_device_philox_matches_oracle():
 
 def test_device_euc2d_matches_oracle():
     rng = np.random.default_rng(2)
-    cnt = 20000
+    cnt = 60000
     inp = rng.integers(0, 1 << 24, size=(cnt, 4)).astype(np.int32)
     inp[:100] = rng.integers(0, 50, size=(100, 4))  # small distances and zeros
     inp[100:110] = [[0, 0, (1 << 24) - 1, (1 << 24) - 1]] * 10  # the largest distance
+    # next to a half-integer: (dx, dy) = (k, isqrt(k) + t) puts dx^2 + dy^2
+    # around k^2 + k, the boundary between rounding to k and to k + 1, for
+    # costs from 1 to 2^24 (the library's fast path covers costs below ~10^6
+    # and |dx|, |dy| < 2^22; the rest take the exact integer steps)
+    k = np.unique(np.exp(rng.uniform(0, np.log((1 << 24) - 1), 8000)).astype(np.int64))
+    near = []
+    for t in (-1, 0, 1):
+        dy = np.floor(np.sqrt(k.astype(np.float64))).astype(np.int64) + t
+        ok = (dy >= 0) & (dy < (1 << 24))
+        near.append(np.stack([np.zeros(ok.sum()), np.zeros(ok.sum()), k[ok], dy[ok]], 1))
+    near = np.concatenate(near).astype(np.int32)
+    near[1::2] = near[1::2][:, [2, 3, 0, 1]]  # both signs of dx, dy
+    inp[200:200 + len(near)] = near
+    # short edges in every direction around a point (the common case)
+    inp[20000:30000, :2] = 5_000_000
+    inp[20000:30000, 2:] = 5_000_000 + rng.integers(-3000, 3000, size=(10000, 2))
     out = np.zeros(cnt, np.int32)
     device_selftest(1, inp, out, cnt)
     want = [oracle.euc2d(np.array([[a, b], [c, d]], np.int32), 0, 1) for a, b, c, d in inp]
