@@ -13,24 +13,32 @@ colony update), and the global-best tour copied to a device buffer.
             pinned host coordinates, faco_iterate, faco_best into a host
             array), host<->device copies inside the timed region;
   roofline  the per-ant kernel (construction + local search), timed live
-            with CUDA events around each launch; achieved = algorithmic
-            bytes / kernel time against the measured HBM copy bandwidth;
-  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+            with CUDA events around each launch: achieved = algorithmic
+            bytes / kernel time against the measured HBM copy bandwidth,
+            beside the DRAM and L2 rates of the recorded ncu counters (L2
+            against the L2 read bandwidth probed in the same run);
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload:
+            its set-up in full, a few warm-up iterations, then one measured
+            iteration on all host cores and one on a single thread.
 
 L2 is flushed (a 512 MB write) before every timed step.  Under torchrun each
 rank solves its own copy of the instance (independent colonies, no data-path
 collective): weak scaling.
 
-Two more sections ride on the same line (both on by default, --sections):
+More sections ride on the same line (all on by default, --sections):
+  uniform1k     the n = 1,000 workload (32 ants, 200 iterations) in full on
+                the GPU, and the oracle's full run on one and on all cores;
+  stippled200k  the n = 200,000 workload (256 blobs, 2,048 ants, 50
+                iterations): throughput, roofline and an oracle sample;
   batched   512 independent instances (n log-uniform in [200, 20,000], 64
             ants, 100 iterations) as one Batch -- one graph launch for the
             budget -- vs. the plain one-Colony-at-a-time loop on a
-            stratified sample of the same instances (instances/s);
+            stratified sample of the same instances (instances/s), the
+            tuner's per-class timings and the all-segment-table plan;
   served    a Poisson stream of requests (n log-uniform in [1,000,
-            100,000], 256 ants, 50 iterations) through the Server vs. the
-            plain loop on the same trace (p50/p99 time-to-budget,
-            instances/s).
-Each carries its own oracle timing on a bounded sample.
+            100,000], 256 ants, 50 iterations) through the Server at rates
+            1..200 per second vs. the plain loop on the same trace (p50/p99
+            time-to-budget, instances/s).
 
 --impl reference times the CPU oracle instead (the method's plain
 statement, test infrastructure) on a bounded sample of the same workload.
@@ -161,63 +169,242 @@ def ants_sources_hash() -> str:
 
 
 def recorded_traffic():
-    """DRAM bytes per launch of the per-ant kernel from one ncu capture, or
-    None when the kernel changed since."""
+    """ncu counters of one launch of the per-ant kernel on the n = 100,000
+    workload (DRAM bytes, L2 bytes), or None when the kernel changed since."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
         if rec.get("sources_sha256") == ants_sources_hash():
-            return float(rec["dram_bytes_per_launch"])
+            return float(rec["dram_bytes_per_launch"]), float(rec["lts_bytes_per_launch"])
     except Exception:
         pass
     return None
 
 
-def oracle_sample(xy, ants, iters, k, sample_ants, sample_iters, threads):
-    """Times the oracle's set-up and `sample_iters` iterations of
-    `sample_ants` ants; returns the full-job throughput implied by them."""
+def oracle_steady(xy, k, threads, warm_ants=32, warm_iters=8, sample_all=256, sample_single=16, seed=1):
+    """Times the oracle on one instance: its set-up in full (all cores),
+    `warm_iters` untimed iterations of `warm_ants` ants (the source moves
+    off the initial tour, as in the steady state), then one iteration of
+    `sample_all` ants on all cores and one of `sample_single` ants on one
+    thread.  Returns (set-up s, s per ant-solution all cores, s per
+    ant-solution single thread)."""
     import oracle
 
     t0 = time.perf_counter()
-    col = oracle.Colony(xy, k, threads=threads)
-    t_create = time.perf_counter() - t0
+    col = oracle.Colony(xy, k, threads=threads, seed=seed)
+    t_setup = time.perf_counter() - t0
+    if warm_iters:
+        col.iterate(warm_ants, warm_iters)
     t0 = time.perf_counter()
-    col.iterate(sample_ants, sample_iters)
-    t_iter = (time.perf_counter() - t0) / (sample_iters * sample_ants)  # seconds per ant-solution
+    col.iterate(sample_all, 1)
+    t_all = (time.perf_counter() - t0) / sample_all
+    col.set_threads(1)
+    t0 = time.perf_counter()
+    col.iterate(sample_single, 1)
+    t_one = (time.perf_counter() - t0) / sample_single
     col.close()
-    t_job = t_create + t_iter * ants * iters
-    return ants * iters / t_job, t_create, t_iter
+    return t_setup, t_all, t_one
+
+
+def cpu_baseline_line(xy, ants, iters, k, threads, **kw):
+    """cpu_baseline object: the oracle's whole-job throughput on all cores,
+    estimated from its measured set-up and a measured steady iteration
+    sample (labelled as such), with the single-thread rate beside it."""
+    t_setup, t_all, t_one = oracle_steady(xy, k, threads, **kw)
+    sa, so = kw.get("sample_all", 256), kw.get("sample_single", 16)
+    v = ants * iters / (t_setup + ants * iters * t_all)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "extrapolated": True,
+            "sample": "oracle set-up of the full instance measured (%.2f s, %d threads); after %d warm-up "
+                      "iterations of %d ants, one iteration of %d ants measured on all cores (%.3f ms per "
+                      "ant-solution) and one of %d ants on one thread (%.3f ms); value = %d ants x %d "
+                      "iterations / (set-up + that many ant-solutions at the all-core rate)" % (
+                          t_setup, threads, kw.get("warm_iters", 8), kw.get("warm_ants", 32), sa,
+                          t_all * 1e3, so, t_one * 1e3, ants, iters),
+            "setup_s": t_setup,
+            "all_cores": {"ant_solutions_per_s": 1.0 / t_all, "cores": threads, "sample_ants": sa},
+            "single_thread": {"ant_solutions_per_s": 1.0 / t_one, "cores": 1, "sample_ants": so,
+                              "note": "iterations only, set-up excluded"}}
 
 
 def run_reference(args, W):
-    """The CPU oracle as the reference arm (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only): its set-up of the
+    full instance and a few warm-up iterations first (untimed), then each
+    step is one iteration of --ref-ants ants on all host cores, timed; value
+    = ant-solutions per second of those iterations (set-up excluded, which
+    favours the oracle against the GPU line, whose steps include set-up)."""
     from paper_2203_02228_gb300 import inputs
 
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
+
     xy = inputs.workload_points(args.workload)
     threads = host_cores()
-    vals = []
+    ref_ants = getattr(args, "ref_ants", 128)
+    warm_iters = getattr(args, "ref_warm_iters", 8)
+    t0 = time.perf_counter()
+    col = oracle.Colony(xy, 16, threads=threads)
+    t_setup = time.perf_counter() - t0
+    col.iterate(32, warm_iters)
+    times = []
     for s in range(args.warmup + args.steps):
-        v, tc, ti = oracle_sample(xy, W["ants"], W["iters"], 16, args.ref_ants, 1, threads)
+        t0 = time.perf_counter()
+        col.iterate(ref_ants, 1)
+        dt = time.perf_counter() - t0
         if s >= args.warmup:
-            vals.append(v)
-    v = statistics.mean(vals)
-    sample = ("per step: oracle set-up of the full instance + 1 iteration of %d ants; value = "
-              "ants*iterations / (set-up + per-ant time * %d ants * %d iterations)") % (
-        args.ref_ants, W["ants"], W["iters"])
+            times.append(dt)
+    col.close()
+    t_step = statistics.mean(times)
+    v = ref_ants / t_step
+    full = W["ants"] * W["iters"] / (t_setup + W["ants"] * W["iters"] * t_step / ref_ants)
+    sample = ("set-up of the full instance (%.2f s) and %d warm-up iterations of 32 ants untimed; each step = one "
+              "iteration of %d ants on %d threads, measured; value = ant-solutions/s of the steps (set-up "
+              "excluded)" % (t_setup, warm_iters, ref_ants, threads))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": W["ants"] * W["iters"] / v * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+int64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": W["n"], "ants": W["ants"], "iterations": W["iters"],
-                   "k": 16, "seed": 1},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+                   "k": 16, "seed": 1, "step": "one iteration of %d ants" % ref_ants},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "setup_s": t_setup, "full_job_estimate": full},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def roofline_line(kernel, n, ants, iters, ants_ms, ants_launches, algo_bytes, peak, peak_src, l2_peak,
+                  traffic=None):
+    """The per-ant kernel's roofline object (see the module docstring)."""
+    if not ants_launches:
+        return None
+    t = ants_ms / ants_launches / 1e3  # s per launch
+    achieved = algo_bytes / ants_launches / t / 1e9
+    r = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
+         "peak_source": "%s HBM copy bandwidth" % peak_src, "unit": "GB/s", "frac": achieved / peak,
+         "achieved_kind": "algorithmic bytes per launch (explicit route/pos arrays per ant, the paper's "
+                          "representation) / live CUDA-event launch time",
+         "traffic": traffic[0] if traffic else None, "avg_launch_ms": t * 1e3,
+         "algorithmic_bytes_per_launch": algo_bytes / ants_launches, "l2_peak": l2_peak,
+         "l2_peak_source": "faco_l2_probe in this run (48 MiB resident, 16-byte L1-bypassing reads)"}
+    if traffic:
+        r["dram_gbs"] = traffic[0] / t / 1e9
+        r["dram_frac"] = r["dram_gbs"] / peak
+        r["l2_bytes_per_launch"] = traffic[1]
+        r["l2_gbs"] = traffic[1] / t / 1e9
+        r["l2_frac"] = r["l2_gbs"] / l2_peak if l2_peak else None
+    return r
+
+
+def algorithmic_bytes(n, ants, iters, st):
+    """Bytes the paper's explicit-array construction + local search must
+    move: route+pos per ant (16n), two 64-byte candidate rows plus 16 bytes
+    of visited/route per roulette step, 16 B per reversed element, 2k x 20 B
+    per local-search pop."""
+    return 16 * n * ants * iters + 208 * st.aco_steps + 16 * st.flip_elems + 640 * st.ls_pops
+
+
+def bench_colony(xy, ants, iters, steps, warmup, stream, flush, barrier, dev):
+    """Full solves of one instance (set-up from device coordinates +
+    budget + best tour to a device buffer): step times, per-ant kernel
+    time and launches, algorithmic bytes and launch counts of the timed
+    steps."""
+    import torch
+
+    from paper_2203_02228_gb300 import Colony
+
+    n = xy.shape[0]
+    xy_dev = torch.from_numpy(xy).to(dev)
+    tour_dev = torch.empty(n, dtype=torch.int32, device=dev)
+    len_dev = torch.empty(1, dtype=torch.int64, device=dev)
+
+    def solve(profile):
+        col = Colony(xy_dev, 16, device=True, stream=stream)
+        if profile:
+            col.profile(True)
+        col.iterate(ants, iters)
+        col.best_device(tour_dev, len_dev)
+        st = col.stats()
+        prof = col.profile_read() if profile else (0.0, 0)
+        col.close()
+        return st, prof
+
+    for _ in range(warmup):
+        solve(False)
+    barrier()
+    out = {"step_ms": [], "ants_ms": 0.0, "ants_launches": 0, "algo_bytes": 0, "launches": 0}
+    for _ in range(steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, (pms, pcnt) = solve(True)
+        e1.record(stream)
+        e1.synchronize()
+        out["step_ms"].append(e0.elapsed_time(e1))
+        out["ants_ms"] += pms
+        out["ants_launches"] += pcnt
+        out["launches"] += st.kernel_launches
+        out["algo_bytes"] += algorithmic_bytes(n, ants, iters, st)
+        out["best_length"] = int(len_dev.item())
+    return out
+
+
+def bench_uniform1k(args, stream, flush, barrier, dev):
+    """The n = 1,000 workload in full: the GPU (set-up + 32 ants x 200
+    iterations, CUDA events) and the oracle's full run, measured, on one
+    thread and on all host cores."""
+    from paper_2203_02228_gb300 import inputs
+
+    W = inputs.WORKLOADS["uniform1k"]
+    xy = inputs.workload_points("uniform1k")
+    r = bench_colony(xy, W["ants"], W["iters"], 5, 2, stream, flush, barrier, dev)
+    ms = statistics.mean(r["step_ms"])
+    out = {"workload": "uniform1k", "n": W["n"], "ants": W["ants"], "iterations": W["iters"], "metric": METRIC,
+           "unit": UNIT, "value": W["ants"] * W["iters"] / (ms / 1e3), "ms_per_step": ms, "steps": 5,
+           "best_length": r["best_length"]}
+    if not args.no_cpu:
+        import oracle
+
+        res = {}
+        for th in (1, host_cores()):
+            t0 = time.perf_counter()
+            col = oracle.Colony(xy, 16, threads=th)
+            col.iterate(W["ants"], W["iters"])
+            L = col.best()[1]
+            col.close()
+            res[th] = (time.perf_counter() - t0, L)
+        t1, tn = res[1][0], res[host_cores()][0]
+        out["cpu_baseline"] = {
+            "value": W["ants"] * W["iters"] / tn, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "extrapolated": False, "sample": "the whole workload (set-up + 32 ants x 200 iterations), measured",
+            "single_thread": {"ant_solutions_per_s": W["ants"] * W["iters"] / t1, "cores": 1, "seconds": t1},
+            "all_cores": {"ant_solutions_per_s": W["ants"] * W["iters"] / tn, "cores": host_cores(), "seconds": tn},
+            "same_best_length_as_gpu": bool(res[1][1] == r["best_length"] == res[host_cores()][1])}
+    return out
+
+
+def bench_stippled200k(args, stream, flush, barrier, dev, peak, peak_src, l2_peak):
+    """The n = 200,000 workload (2,048 ants, 50 iterations): full solves on
+    the GPU with the per-ant kernel's roofline, and an oracle sample."""
+    from paper_2203_02228_gb300 import inputs
+
+    W = inputs.WORKLOADS["stippled200k"]
+    xy = inputs.workload_points("stippled200k")
+    n, ants, iters = xy.shape[0], W["ants"], W["iters"]
+    r = bench_colony(xy, ants, iters, args.c3_steps, 1, stream, flush, barrier, dev)
+    ms = statistics.mean(r["step_ms"])
+    out = {"workload": "stippled200k", "n": n, "ants": ants, "iterations": iters, "metric":
+           "ant-solutions/sec at 200k nodes", "unit": UNIT, "value": ants * iters / (ms / 1e3), "ms_per_step": ms,
+           "steps": args.c3_steps, "gpu_launches": r["launches"], "best_length": r["best_length"],
+           "roofline": roofline_line("k_ants_blk<16> (construction + local search)", n, ants, iters, r["ants_ms"],
+                                     r["ants_launches"], r["algo_bytes"], peak, peak_src, l2_peak)}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_line(xy, ants, iters, 16, host_cores())
+    return out
 
 
 def bench_batched(args, stream, flush, barrier):
@@ -260,6 +447,26 @@ def bench_batched(args, stream, flush, barrier):
         launches = b.stats(0).kernel_launches
         b.close()
     t_batch = statistics.mean(wall)
+    from paper_2203_02228_gb300 import tuner_report
+
+    tuned = [r for r in tuner_report() if r["goal"] == "batch" and r["ants"] == ants]
+
+    # the same batch with every colony on segment tables (no tuner), timed
+    # the same way, to show what the tuner's choice is worth
+    def run_fixed(mode):
+        b = Batch(xs, k, seeds=seeds, stream=stream)
+        b.set_plan(mode)
+        b.iterate(ants, iters)
+        tours, lens = b.tours()
+        b.close()
+        return lens
+
+    run_fixed(0)
+    flush.zero_()
+    barrier()
+    t0 = time.perf_counter()
+    lens_tab = run_fixed(0)
+    t_tab = time.perf_counter() - t0
 
     # plain loop on every 8th instance by size: the sample spans the size range
     order = np.argsort(ns, kind="stable")
@@ -313,22 +520,47 @@ def bench_batched(args, stream, flush, barrier):
         "plan": {"colonies_per_kernel": {name: int((plan == v).sum()) for v, name in
                                          enumerate(("segment_table", "arrays_2_blocks_per_sm", "arrays_4_blocks_per_sm",
                                                     "arrays_8_blocks_per_sm"))}},
+        "tuner_ms_per_class": tuned,
+        "all_segment_tables": {"value": len(xs) / t_tab, "unit": "instances/s", "seconds": t_tab,
+                               "equal_lengths": bool(np.array_equal(lens_tab, lens))},
         "gpu_launches_per_batch": int(launches), "graph_launches_per_batch": 1, "cpu_baseline": cpu,
         "h2d_bytes_per_batch": int(8 * ns.sum()), "d2h_bytes_per_batch": int(4 * ns.sum() + 8 * len(xs)),
     }
 
 
+def serve_plan(rates, requests):
+    """Requests per rate: `requests` where the stream saturates the GPU,
+    fewer at the lowest rates so that each trace arrives within ~30 s."""
+    return [(r, int(min(requests, max(30, round(30 * r))))) for r in rates]
+
+
+def plain_loop_times(arrivals, service):
+    """First-come-first-served completion times of one instance at a time:
+    C_i = max(A_i, C_{i-1}) + S_i."""
+    done, t = [], 0.0
+    for a_i, s_i in zip(arrivals, service):
+        t = max(t, a_i) + s_i
+        done.append(t)
+    return np.array(done)
+
+
 def bench_served(args, stream, barrier):
-    """A Poisson stream of requests (n log-uniform in [1e3, 1e5], 256 ants,
+    """Poisson streams of requests (n log-uniform in [1e3, 1e5], 256 ants,
     50 iterations) through the server -- admission by device memory,
-    continuous batching -- and the same arrival trace through the plain
-    loop (one Colony at a time, first come first served).  Time-to-budget
-    = completion - arrival, host clock."""
+    continuous batching -- at each rate, and the plain loop (one Colony at
+    a time, first come first served) on the same traces.  Time-to-budget =
+    completion - arrival, host clock.  The plain loop's service time of
+    each request is measured once (each instance solved alone, one after
+    another on the idle GPU, through the public API); its completions on a
+    trace follow from the arrivals by the FCFS recursion."""
     import threading as th
 
     from paper_2203_02228_gb300 import Colony, Server, inputs
 
     w = inputs.SERVE_WORKLOADS["serve100k"]
+    plan = serve_plan(args.serve_rates, args.serve_requests)
+    nmax = max(c for _, c in plan)
+    xs, seeds, _ = inputs.serve_trace("serve100k", nmax, 1.0)
     out = {"workload": "serve100k", "ants": w["ants"], "iterations": w["iters"], "k": w["k"],
            "n_range": [w["lo"], w["hi"]], "metric": "time-to-budget p50/p99 (s), instances/sec",
            "pool_bytes": args.serve_pool_gb << 30, "rates": []}
@@ -336,20 +568,32 @@ def bench_served(args, stream, barrier):
     with Server(1 << 30) as s:
         for j, n in enumerate((1500, 6000, 30000)):
             s.wait(s.submit(inputs.uniform(n, seed=j), w["k"], w["ants"], 2, 1))
-    for rate in args.serve_rates:
-        xs, seeds, arr = inputs.serve_trace("serve100k", args.serve_requests, rate)
-        # served
+    # plain loop: each request alone, once
+    barrier()
+    service, plens = [], []
+    for i, x in enumerate(xs):
+        t0 = time.perf_counter()
+        c = Colony(x, w["k"], seed=int(seeds[i]), stream=stream)
+        c.iterate(w["ants"], w["iters"])
+        _, L = c.best()
+        c.close()
+        service.append(time.perf_counter() - t0)
+        plens.append(L)
+    out["plain_service_s"] = {"mean": float(np.mean(service)), "p50": float(np.median(service)),
+                              "max": float(np.max(service)), "requests": len(service)}
+    for rate, count in plan:
+        _, _, arr = inputs.serve_trace("serve100k", count, rate)
         barrier()
         with Server(args.serve_pool_gb << 30) as s:
             t0 = time.perf_counter()
-            tickets = [None] * len(xs)
+            tickets = [None] * count
 
             def feed():
-                for i, x in enumerate(xs):
+                for i in range(count):
                     d = t0 + arr[i] - time.perf_counter()
                     if d > 0:
                         time.sleep(d)
-                    tickets[i] = s.submit(x, w["k"], w["ants"], w["iters"], int(seeds[i]))
+                    tickets[i] = s.submit(xs[i], w["k"], w["ants"], w["iters"], int(seeds[i]))
 
             f = th.Thread(target=feed)
             f.start()
@@ -359,36 +603,21 @@ def bench_served(args, stream, barrier):
         lat = np.array([(r[3] - r[2]) / 1e9 for r in res])
         span = (max(r[3] for r in res) - min(r[2] for r in res)) / 1e9
         served = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                  "mean_s": float(lat.mean()), "instances_per_s": len(xs) / span,
-                  "ant_solutions_per_s": len(xs) * w["ants"] * w["iters"] / span,
+                  "mean_s": float(lat.mean()), "instances_per_s": count / span,
+                  "ant_solutions_per_s": count * w["ants"] * w["iters"] / span,
                   "peak_active": st["peak_active"], "rounds": st["rounds"],
                   "gpu_launches": st["kernel_launches"], "mean_best_length": float(np.mean([r[1] for r in res]))}
-        # plain loop, same trace: one instance at a time in arrival order
-        barrier()
-        t0 = time.perf_counter()
-        plat, plens = [], []
-        for i, x in enumerate(xs):
-            d = t0 + arr[i] - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            c = Colony(x, w["k"], seed=int(seeds[i]), stream=stream)
-            c.iterate(w["ants"], w["iters"])
-            tour, L = c.best()
-            c.close()
-            plat.append(time.perf_counter() - (t0 + arr[i]))
-            plens.append(L)
-        pspan = time.perf_counter() - t0
-        plat = np.array(plat)
+        done = plain_loop_times(arr, service[:count])
+        plat = done - arr
         plain = {"p50_s": float(np.percentile(plat, 50)), "p99_s": float(np.percentile(plat, 99)),
-                 "mean_s": float(plat.mean()), "instances_per_s": len(xs) / pspan}
-        out["rates"].append({"rate_per_s": rate, "requests": len(xs), "served": served, "plain_loop": plain,
-                             "equal_lengths": bool(np.array_equal([r[1] for r in res], plens))})
+                 "mean_s": float(plat.mean()), "instances_per_s": count / (done[-1] - arr[0])}
+        out["rates"].append({"rate_per_s": rate, "requests": count, "served": served, "plain_loop": plain,
+                             "equal_lengths": bool(np.array_equal([r[1] for r in res], plens[:count]))})
     if not args.no_cpu:
         # the oracle on three requests of the trace (10th, 50th, 90th size
         # percentile): set-up + 1 iteration of 32 ants, scaled to 256 ants x 50
         import oracle
 
-        xs, seeds, _ = inputs.serve_trace("serve100k", args.serve_requests, args.serve_rates[0])
         ns = np.array([x.shape[0] for x in xs])
         order = np.argsort(ns)
         pick = [order[int(q * (len(xs) - 1))] for q in (0.1, 0.5, 0.9)]
@@ -402,9 +631,10 @@ def bench_served(args, stream, barrier):
             col.close()
             t_sum += (t1 - t0) + w["iters"] * (t2 - t1) * w["ants"] / 32
         out["cpu_baseline"] = {"value": len(pick) / t_sum, "unit": "instances/s", "cores": host_cores(),
-                               "kind": "oracle", "sample": "3 requests (10th/50th/90th size percentile, n = %s): "
-                               "oracle set-up + 1 iteration of 32 ants, scaled to %d ants x %d iterations; one "
-                               "request at a time" % ([int(ns[i]) for i in pick], w["ants"], w["iters"])}
+                               "kind": "oracle", "extrapolated": True,
+                               "sample": "3 requests (10th/50th/90th size percentile, n = %s): oracle set-up + 1 "
+                               "iteration of 32 ants measured, scaled to %d ants x %d iterations; one request "
+                               "at a time" % ([int(ns[i]) for i in pick], w["ants"], w["iters"])}
     return out
 
 
@@ -417,12 +647,15 @@ def main():
     ap.add_argument("--workload", default="stippled100k")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ref-ants", type=int, default=32)
+    ap.add_argument("--ref-ants", type=int, default=128, help="ants per step of the reference arm")
+    ap.add_argument("--ref-warm-iters", type=int, default=8)
     ap.add_argument("--iters", type=int, default=0, help="override the iteration budget (testing only)")
-    ap.add_argument("--sections", default="main,batch,serve", help="comma list of: main, batch, serve")
+    ap.add_argument("--sections", default="main,uniform1k,stippled200k,batch,serve",
+                    help="comma list of: main, uniform1k, stippled200k, batch, serve")
+    ap.add_argument("--c3-steps", type=int, default=2)
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2.0, 8.0])
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1, 2, 5, 10, 20, 50, 100, 200])
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-pool-gb", type=int, default=64)
     args = ap.parse_args()
     sections = set(args.sections.split(","))
@@ -438,7 +671,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2203_02228_gb300 import Colony, build
+    from paper_2203_02228_gb300 import build, l2_probe
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -449,12 +682,6 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-
-    xy = inputs.workload_points(args.workload)
-    n, ants, iters = xy.shape[0], W["ants"], W["iters"]
-    xy_dev = torch.from_numpy(xy).to(dev)
-    tour_dev = torch.empty(n, dtype=torch.int32, device=dev)
-    len_dev = torch.empty(1, dtype=torch.int64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -462,59 +689,33 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def solve(profile=False):
-        col = Colony(xy_dev, 16, device=True, stream=stream)
-        if profile:
-            col.profile(True)
-        col.iterate(ants, iters)
-        col.best_device(tour_dev, len_dev)
-        st = col.stats()
-        prof = col.profile_read() if profile else (0.0, 0)
-        col.close()
-        return st, prof
+    peak, peak_src = load_peaks()
+    l2_peak = max(l2_probe(48 << 20, 200) for _ in range(3))
+    extra = {}
 
     if "main" not in sections:
-        out = {}
+        if "uniform1k" in sections:
+            extra["uniform1k"] = bench_uniform1k(args, stream, flush, barrier, dev)
+        if "stippled200k" in sections:
+            extra["stippled200k"] = bench_stippled200k(args, stream, flush, barrier, dev, peak, peak_src, l2_peak)
         if "batch" in sections:
-            out["batched"] = bench_batched(args, stream, flush, barrier)
+            extra["batched"] = bench_batched(args, stream, flush, barrier)
         if "serve" in sections:
-            out["served"] = bench_served(args, stream, barrier)
+            extra["served"] = bench_served(args, stream, barrier)
         if rank == 0:
-            print(json.dumps(out), flush=True)
+            print(json.dumps(extra), flush=True)
         return
 
-    for _ in range(args.warmup):
-        solve()
-    barrier()
+    xy = inputs.workload_points(args.workload)
+    n, ants, iters = xy.shape[0], W["ants"], W["iters"]
 
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms = []
-    ants_ms = 0.0
-    ants_launches = 0
-    algo_bytes = 0
-    launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st, (pms, pcnt) = solve(profile=True)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        ants_ms += pms
-        ants_launches += pcnt
-        launches += st.kernel_launches
-        # algorithmic bytes of the per-ant kernel: explicit route+pos per ant
-        # (16n), source rows per roulette step (2 x 64 B + visited/route 16 B),
-        # 16 B per reversed element, 2k x 20 B per local-search pop.
-        algo_bytes += (16 * n * ants * iters + 208 * st.aco_steps + 16 * st.flip_elems + 640 * st.ls_pops)
+    r = bench_colony(xy, ants, iters, args.steps, args.warmup, stream, flush, barrier, dev)
     barrier()
     clk = clocks.stop()
 
-    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
+    ms = max_over_ranks(statistics.mean(r["step_ms"]), world, dev)
     value = job_throughput(ants * iters, world, ms)
 
     # end to end through the host API (pinned host coordinates, host tour)
@@ -526,7 +727,7 @@ def main():
         p = _lib.params_default()
         p.stream = stream.cuda_stream
         e2e_ms = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, min(args.steps, 5))):
             flush.zero_()
             barrier()
             t0 = time.perf_counter()
@@ -540,26 +741,23 @@ def main():
         e2e = {"value": job_throughput(ants * iters, world, em), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": 4 * n + 8, "ms_per_step": em}
 
-    peak, peak_src = load_peaks()
-    achieved = (algo_bytes / ants_launches) / (ants_ms / ants_launches / 1e3) / 1e9 if ants_launches else None
-    roofline = {"kernel": "k_ants_blk (construction + local search)", "bound": "hbm", "achieved": achieved,
-                "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
-                "avg_launch_ms": ants_ms / ants_launches if ants_launches else None,
-                "algorithmic_bytes_per_launch": algo_bytes / ants_launches if ants_launches else None}
+    roofline = roofline_line("k_ants_blk<16> (construction + local search)", n, ants, iters, r["ants_ms"],
+                             r["ants_launches"], r["algo_bytes"], peak, peak_src, l2_peak,
+                             recorded_traffic() if args.workload == "stippled100k" else None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, tc, ti = oracle_sample(xy, ants, iters, 16, 32, 1, host_cores())
-        cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": "oracle set-up of the full instance (%.1f s) + 1 iteration of 32 ants (%.1f ms per "
-                         "ant-solution), extrapolated to %d ants x %d iterations" % (tc, ti * 1e3, ants, iters)}
+        cpu = cpu_baseline_line(xy, ants, iters, 16, host_cores())
 
-    batched = served = None
-    if "batch" in sections and world == 1:
-        batched = bench_batched(args, stream, flush, barrier)
-    if "serve" in sections and world == 1:
-        served = bench_served(args, stream, barrier)
+    if world == 1:
+        if "uniform1k" in sections:
+            extra["uniform1k"] = bench_uniform1k(args, stream, flush, barrier, dev)
+        if "stippled200k" in sections:
+            extra["stippled200k"] = bench_stippled200k(args, stream, flush, barrier, dev, peak, peak_src, l2_peak)
+        if "batch" in sections:
+            extra["batched"] = bench_batched(args, stream, flush, barrier)
+        if "serve" in sections:
+            extra["served"] = bench_served(args, stream, barrier)
 
     if rank == 0:
         line = {
@@ -569,9 +767,10 @@ def main():
             "config": {"workload": args.workload, "n": n, "ants": ants, "iterations": iters, "k": 16,
                        "seed": 1, "l2": "flushed before every step (512 MB write)",
                        "parallelism": "independent colonies per rank" if world > 1 else "single colony"},
-            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clk, "batched": batched, "served": served,
+            "e2e": e2e, "gpu_launches": r["launches"], "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -99,6 +99,20 @@ int faco_batch_set_plan(faco_batch* b, int32_t mode);
  * -1 before the first faco_batch_iterate. */
 int faco_batch_get_plan(faco_batch* b, int32_t* variants);
 
+/* The kernel tuner's measurements on the current device (host data; the
+ * tuner runs inside the first faco_batch_iterate of a batch whose size
+ * classes are new to the process, and inside the server).  One row of 9
+ * doubles per tuned (size class, ants, roulette width, goal): the class
+ * (0: n < 512; c >= 1: 512 * 4^(c-1) <= n < 512 * 4^c), ants per
+ * iteration, roulette width (16 or 32), goal (0
+ * batch throughput, 1 one request's latency), the chosen code (0 segment
+ * table, 1/2/3 arrays at 2/4/8 resident blocks per SM), then the four
+ * codes' timings in ms -- one iteration of up to 64 colonies of the class,
+ * scaled for goal 0 by the share of the GPU's resident ant slots the class
+ * holds; -1 where a code was not tried.  Writes min(max_rows, recorded)
+ * rows and the recorded count into *count.  Errors: FACO_E_ARG. */
+int faco_batch_tuner_report(double* rows, int32_t max_rows, int32_t* count);
+
 void faco_batch_destroy(faco_batch* b);
 
 #ifdef __cplusplus

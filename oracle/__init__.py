@@ -115,6 +115,8 @@ def lib():
             L.orc_get_ant_pre.argtypes = [vp, vp, vp, vp, vp]
             L.orc_set_state.restype = ctypes.c_int
             L.orc_set_state.argtypes = [vp, vp, vp]
+            L.orc_set_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [vp, ctypes.c_int32]
             _lib = L
     return _lib
 
@@ -303,6 +305,10 @@ class Colony:
         if rc != 0:
             raise ValueError("keep_pre_ls was not set")
         return t, lens, [chk[i, :nchk[i]].copy() for i in range(m)]
+
+    def set_threads(self, threads: int) -> None:
+        if self._L.orc_set_threads(self._h, int(threads)) != 0:
+            raise ValueError("threads must be >= 1")
 
     def set_state(self, tau=None, src_route=None):
         tau = None if tau is None else np.ascontiguousarray(tau, dtype=np.float32)

@@ -900,3 +900,9 @@ int orc_set_state(orc_colony* C, const float* tau, const int32_t* src_route) {
   }
   return ORC_OK;
 }
+
+int orc_set_threads(orc_colony* C, int32_t threads) {
+  if (!C || threads < 1) return ORC_E_ARG;
+  C->prm.threads = threads;
+  return ORC_OK;
+}

@@ -111,6 +111,9 @@ int orc_get_ant_pre(const orc_colony* c, int32_t* tours, int64_t* lens,
                     int32_t* checklists /* ants x n */, int32_t* nchecks);
 /* Overwrites the pheromone and the source (a test hook for fixed-point checks). */
 int orc_set_state(orc_colony* c, const float* tau, const int32_t* src_route);
+/* OpenMP threads used by later orc_iterate calls (>= 1); results do not
+ * depend on it (ants are independent within an iteration). */
+int orc_set_threads(orc_colony* c, int32_t threads);
 
 #ifdef __cplusplus
 }

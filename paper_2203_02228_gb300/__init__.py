@@ -391,6 +391,23 @@ class Server:
         return {f: getattr(st, f) for f, _ in st._fields_}
 
 
+def tuner_report(max_rows: int = 256) -> list:
+    """The batch/server kernel tuner's timings on the current device (see
+    faco_batch_tuner_report): one dict per tuned size class."""
+    rows = np.zeros((max_rows, 9), np.float64)
+    cnt = ctypes.c_int32()
+    _lib.check(load().faco_batch_tuner_report(_ptr(rows), max_rows, ctypes.byref(cnt)), "faco_batch_tuner_report")
+    names = ("segment_table", "arrays_2_blocks_per_sm", "arrays_4_blocks_per_sm", "arrays_8_blocks_per_sm")
+    out = []
+    for r in rows[:min(cnt.value, max_rows)]:
+        c = int(r[0])
+        out.append({"size_class": c, "n_range": [0 if c == 0 else 512 * 4 ** (c - 1), 512 * 4 ** c - 1],
+                    "ants": int(r[1]), "roulette_width": int(r[2]), "goal": ("batch", "latency")[int(r[3])],
+                    "chosen": names[int(r[4])] if r[4] >= 0 else None,
+                    "ms": {nm: (float(v) if v >= 0 else None) for nm, v in zip(names, r[5:9])}})
+    return out
+
+
 def l2_probe(bytes_: int = 48 << 20, reps: int = 200) -> float:
     """L2 read bandwidth of the current device in GB/s (see faco_l2_probe)."""
     g = ctypes.c_double()

@@ -138,6 +138,7 @@ def load():
             "faco_batch_set_plan": (ctypes.c_int, [vp, i32]),
             "faco_batch_get_plan": (ctypes.c_int, [vp, vp]),
             "faco_batch_destroy": (None, [vp]),
+            "faco_batch_tuner_report": (ctypes.c_int, [vp, i32, P(i32)]),
             # include/faco_serve.h
             "faco_server_create": (ctypes.c_int, [ctypes.c_size_t, P(faco_params), P(vp)]),
             "faco_server_request_bytes": (i64, [i32, i32, i32, P(faco_params)]),

@@ -296,6 +296,12 @@ int faco_batch_get_plan(faco_batch* b, int32_t* variants) {
   return FACO_OK;
 }
 
+int faco_batch_tuner_report(double* rows, int32_t max_rows, int32_t* count) {
+  if (!count || max_rows < 0 || (max_rows > 0 && !rows)) return FACO_E_ARG;
+  *count = tuner_report(rows, max_rows);
+  return FACO_OK;
+}
+
 void faco_batch_destroy(faco_batch* b) {
   if (!b) return;
   free_batch(b);

@@ -452,6 +452,9 @@ int Runner::kernels_per_iteration() const {
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune;  // (device, class, m, kw, goal) -> variant
+// the timings behind each choice, per variant (ms, scaled as the goal says;
+// negative: not tried)
+std::map<std::tuple<int, int, int, int, int>, std::vector<float>> g_tune_ms;
 
 int cur_device() {
   int d = 0;
@@ -510,6 +513,8 @@ int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s,
     bool any_tab = false;
     for (const RunEntry& e : v) any_tab |= e.a->cap[e.i] > 0;
     int best = kVarArr2;
+    float t_rec[kNVariants];
+    for (int variant = 0; variant < kNVariants; ++variant) t_rec[variant] = -1.0f;
     {
       float t[kNVariants];
       for (int variant = 0; variant < kNVariants && rc == FACO_OK; ++variant) {
@@ -541,15 +546,45 @@ int tuner_run(const std::vector<RunEntry>& entries, size_t smem, cudaStream_t s,
         t[variant] = (float)(tmin * frac);
       }
       if (rc != FACO_OK) break;
-      for (int variant = 0; variant < kNVariants; ++variant)
+      for (int variant = 0; variant < kNVariants; ++variant) {
         if (t[variant] < t[best]) best = variant;
+        if (t[variant] < 1e29f) t_rec[variant] = t[variant];
+      }
     }
     tuner_put(kv.first.first, kv.first.second, v[0].g->kw, best, goal);
+    if (rc == FACO_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      std::vector<float>& rec =
+          g_tune_ms[std::make_tuple(cur_device(), kv.first.first, kv.first.second, v[0].g->kw, goal)];
+      rec.assign(kNVariants, -1.0f);
+      for (int variant = 0; variant < kNVariants; ++variant) rec[variant] = t_rec[variant];
+    }
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (rc != FACO_OK) (void)cudaGetLastError();
   return rc;
+}
+
+int tuner_report(double* out, int max_rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int dev = cur_device();
+  int r = 0;
+  for (const auto& kv : g_tune_ms) {
+    if (std::get<0>(kv.first) != dev) continue;
+    if (r < max_rows && out) {
+      double* row = out + (size_t)r * (5 + kNVariants);
+      row[0] = std::get<1>(kv.first);
+      row[1] = std::get<2>(kv.first);
+      row[2] = std::get<3>(kv.first);
+      row[3] = std::get<4>(kv.first);
+      auto it = g_tune.find(kv.first);
+      row[4] = it == g_tune.end() ? -1 : it->second;
+      for (int v = 0; v < kNVariants; ++v) row[5 + v] = kv.second[v];
+    }
+    ++r;
+  }
+  return r;
 }
 
 size_t batch_smem_blk(int kw) {

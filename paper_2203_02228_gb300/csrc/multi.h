@@ -122,6 +122,10 @@ void tuner_put(int cls, int m, int kw, int variant, int goal = kTuneBatch);
 // `entries` (per-ant buffers only are written) and records the best for
 // the goal.
 int tuner_run(const std::vector<RunEntry>& entries, size_t smem_blk, cudaStream_t s, int goal = kTuneBatch);
+// Rows of (class, ants, roulette width, goal, chosen variant, the variants'
+// timings in ms) for the current device, up to max_rows into out (5 +
+// kNVariants doubles each); returns the number of rows recorded.
+int tuner_report(double* out, int max_rows);
 
 size_t batch_smem_blk(int kw);
 

@@ -100,3 +100,26 @@ def test_submit_rejects_bad_requests():
         big = inputs.uniform(50000, seed=2)
         with pytest.raises(FacoError):
             s.submit(big, 16, 256, 1, 1)  # can never fit 64 MB
+
+
+def test_served_results_equal_the_oracle():
+    """Requests served in a mix give the oracle's tours and lengths (Alg 2
+    with the request's seed) -- checked against the CPU statement of the
+    method, not only against the one-colony GPU path."""
+    import oracle
+
+    reqs = [(inputs.stippled(900, seed=81, blobs=6, ridges=1, side=50_000), 16, 8, 21),
+            (inputs.uniform(1500, seed=82), 24, 10, 22),
+            (inputs.uniform(420, seed=83), 16, 6, 23),
+            (inputs.uniform(2600, seed=84), 16, 4, 24)]
+    with Server(2 << 30) as s:
+        tickets = [s.submit(xy, 16, ants, budget, seed) for xy, ants, budget, seed in reqs]
+        got = [s.wait(t) for t in tickets]
+        st = s.stats()
+    assert st["peak_active"] >= 2
+    for (xy, ants, budget, seed), g in zip(reqs, got):
+        o = oracle.Colony(xy, 16, seed=seed, threads=8)
+        o.iterate(ants, budget)
+        tour, L = o.best()
+        assert g[1] == L
+        np.testing.assert_array_equal(g[0], tour)
