@@ -73,6 +73,7 @@ struct ArrTour {
     return route[p];
   }
   __device__ __forceinline__ int succ(int x) const { return at_off(pos[x], 1); }
+  __device__ __forceinline__ int succ_w(int x) const { return succ(x); }  // warp-uniform x
   __device__ __forceinline__ int pred(int x) const { return at_off(pos[x], -1); }
   __device__ __forceinline__ int adj(int x, bool up) const { return at_off(pos[x], up ? 1 : -1); }
   __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
@@ -141,10 +142,10 @@ struct ArrTour {
 
 // Exchange tour edges {n1,n2},{n3,n4} for {n1,n3},{n2,n4}: with n1->n2 a
 // forward edge this is the Alg 3 move (n1,n2,n3,n4) -> flip n2..n3,
-// otherwise the move (n2,n1,n4,n3) -> flip n1..n4.
+// otherwise the move (n2,n1,n4,n3) -> flip n1..n4.  Warp-collective.
 template <class Tour>
 __device__ __forceinline__ bool tour_move2(Tour& T, int n1, int n2, int n3, int n4, LsStats& S) {
-  if (T.succ(n1) == n2) return T.flip(n2, n3, S);
+  if (T.succ_w(n1) == n2) return T.flip(n2, n3, S);
   return T.flip(n1, n4, S);
 }
 
@@ -189,14 +190,42 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
       bn0 = T.adj(b, lane < 16);
   }
   const int2 xbn0 = T.coord(bn0), xbn1 = two ? T.coord(bn1) : xa;
-  const int d_as = euc2d(xa, x1), d_ap = euc2d(xp, xa);
+  // the costs within a's tour neighbourhood are the same on every lane:
+  // lane j computes the j-th, shuffles share them
+  //   0 d(a,s1)  1 d(p,a)  2 d(p,s1)  3 d(s1,s2)  4 d(p,s2)  5 d(s2,s3)  6 d(p,s3)
+  int2 cu = xa, cv = x1;
+  if (lane == 1) {
+    cu = xp;
+    cv = xa;
+  } else if (lane == 2) {
+    cu = xp;
+  } else if (lane == 3) {
+    cu = x1;
+    cv = x2;
+  } else if (lane == 4) {
+    cu = xp;
+    cv = x2;
+  } else if (lane == 5) {
+    cu = x2;
+    cv = x3;
+  } else if (lane == 6) {
+    cu = xp;
+    cv = x3;
+  }
+  const int32_t cst = euc2d(cu, cv);
+  const int d_as = __shfl_sync(kFull, cst, 0), d_ap = __shfl_sync(kFull, cst, 1);
   // gains in 32 bits: each is a signed sum of at most six EUC_2D costs of
   // coordinates below 2^24 (each cost below 2^25)
   int32_t rem1 = 0, rem2 = 0, rem3 = 0;
-  if (do_or) {
-    rem1 = d_ap + d_as - euc2d(xp, x1);
-    rem2 = d_ap + euc2d(x1, x2) - euc2d(xp, x2);
-    rem3 = d_ap + euc2d(x2, x3) - euc2d(xp, x3);
+  {
+    const int32_t c2 = __shfl_sync(kFull, cst, 2), c3 = __shfl_sync(kFull, cst, 3),
+                  c4 = __shfl_sync(kFull, cst, 4), c5 = __shfl_sync(kFull, cst, 5),
+                  c6 = __shfl_sync(kFull, cst, 6);
+    if (do_or) {
+      rem1 = d_ap + d_as - c2;
+      rem2 = d_ap + c3 - c4;
+      rem3 = d_ap + c5 - c6;
+    }
   }
   int32_t b2 = 0, bo = 0;
   int i2 = INT_MAX, io = INT_MAX;

@@ -137,6 +137,24 @@ __device__ __forceinline__ int bsearch_le(const int32_t* key, int S, int v) {
   return lo;
 }
 
+// The same search by a whole warp for one (warp-uniform) value: each level
+// compares 32 keys spaced evenly over the remaining range and keeps the
+// last one <= v, so a table of up to 1,024 keys takes two shared-memory
+// round trips instead of ten dependent ones.  Every lane gets the rank.
+__device__ __forceinline__ int bsearch_le_warp(const int32_t* key, int S, int v) {
+  const int lane = lane_id();
+  int lo = 0, len = S;  // the answer lies in [lo, lo + len); key[lo] <= v
+  while (len > 1) {
+    const int st = (len + 31) >> 5;
+    const bool le = lane * st < len && key[lo + lane * st] <= v;
+    const unsigned b = __ballot_sync(kFull, le);
+    const int L = b ? 31 - __clz(b) : 0;
+    lo += L * st;
+    len = min(st, len - L * st);
+  }
+  return lo;
+}
+
 // Insert val at index r of arr[0..S) (warp-collective).
 __device__ __forceinline__ void u16_insert(uint16_t* arr, int S, int r, uint16_t val) {
   const int lane = lane_id();
@@ -164,9 +182,9 @@ __device__ __forceinline__ void segtab_keys(const SegTab& T) {
   __syncwarp();
 }
 
-// Rank in B of segment id (by its lo).
+// Rank in B of segment id (by its lo; warp-collective).
 __device__ __forceinline__ int rank_B(const SegTab& T, int id) {
-  return bsearch_le(T.loB, *T.S, T.sg[id].lo);
+  return bsearch_le_warp(T.loB, *T.S, T.sg[id].lo);
 }
 
 // The two inserts of a split in one pass: (idA, keyA) at index rA of
@@ -245,7 +263,7 @@ __device__ __forceinline__ void del_both(const SegTab& T, int S, int rA, int rB)
 // on entry and on exit.  false: table full.
 static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
   const int S = *T.S;
-  const int r = bsearch_le(T.offA, S, t);
+  const int r = bsearch_le_warp(T.offA, S, t);
   const int id = T.A[r];
   const Seg s = T.sg[id];
   if (s.off == t) return true;
@@ -284,7 +302,7 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   const int ia = T.A[r], ib = T.A[r + 1];
   const Seg a = T.sg[ia], b = T.sg[ib];
   if (!(a.rev == b.rev && (a.rev ? (b.lo + b.len == a.lo) : (a.lo + a.len == b.lo)))) return;
-  const int rbb = bsearch_le(T.loB, S, b.lo);
+  const int rbb = bsearch_le_warp(T.loB, S, b.lo);
   __syncwarp();
   if (lane_id() == 0) {
     T.sg[ia].len = a.len + b.len;
@@ -299,7 +317,7 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   if (ib != last) {
     const Seg sl = T.sg[last];
     const int ra = T.rankA[last];
-    const int rl = bsearch_le(T.loB, S - 1, sl.lo);
+    const int rl = bsearch_le_warp(T.loB, S - 1, sl.lo);
     __syncwarp();
     if (lane_id() == 0) {
       T.sg[ib] = sl;
@@ -354,6 +372,17 @@ struct SegTour {
     const Seg s = T.sg[T.B[r]];
     const int t = s.off + (s.rev ? s.lo + s.len - 1 - q : q - s.lo);
     return (unsigned)t < (unsigned)n ? t : 0;
+  }
+  // pos_of and succ for a warp-uniform argument (warp-collective)
+  __device__ __forceinline__ int pos_of_w(int q) const {
+    const int r = bsearch_le_warp(T.loB, *T.S, q);
+    const Seg s = T.sg[T.B[r]];
+    const int t = s.off + (s.rev ? s.lo + s.len - 1 - q : q - s.lo);
+    return (unsigned)t < (unsigned)n ? t : 0;
+  }
+  __device__ __forceinline__ int succ_w(int q) const {
+    int id = T.B[bsearch_le_warp(T.loB, *T.S, q)];
+    return step_up(q, id);
   }
   __device__ __forceinline__ int at(int t) const {
     const int r = bsearch_le(T.offA, *T.S, t);
@@ -429,7 +458,7 @@ struct SegTour {
   // (the array rule, entry for entry).  false: the table is full.
   __device__ __noinline__ bool flip(int x, int y, LsStats& St) {
     const int lane = lane_id();
-    int i = pos_of(x), j = pos_of(y);
+    int i = pos_of_w(x), j = pos_of_w(y);
     __syncwarp();  // every lane has read the table before any lane rewrites a segment
     int L = j - i;
     if (L < 0) L += n;
@@ -453,8 +482,8 @@ struct SegTour {
     if (i != 0 && !seg_split(T, i)) return false;
     if (j1 != 0 && !seg_split(T, j1)) return false;
     const int S = *T.S;
-    const int ri = bsearch_le(T.offA, S, i);
-    const int rj = (j1 == 0) ? S - 1 : bsearch_le(T.offA, S, j1) - 1;
+    const int ri = bsearch_le_warp(T.offA, S, i);
+    const int rj = (j1 == 0) ? S - 1 : bsearch_le_warp(T.offA, S, j1) - 1;
     if (i <= j) {
       // contiguous ranks ri..rj: new off = i + j + 1 - off - len, direction flips
       const int c = rj - ri + 1;
@@ -523,7 +552,7 @@ struct SegTour {
         const int id = T.tmp[straddle];
         const Seg s = T.sg[id];
         nid = S;
-        const int rb = bsearch_le(T.loB, S, s.lo);
+        const int rb = bsearch_le_warp(T.loB, S, s.lo);
         __syncwarp();
         if (lane == 0) {
           // id keeps ant positions [s.off, n); nid takes [0, s.len - cut)
@@ -578,6 +607,7 @@ struct HybTour {
   __device__ __forceinline__ bool arrays() const { return *mode != 0; }
   __device__ __forceinline__ int pos_of(int x) const { return arrays() ? ar.pos_of(x) : sg.pos_of(x); }
   __device__ __forceinline__ int succ(int x) const { return arrays() ? ar.succ(x) : sg.succ(x); }
+  __device__ __forceinline__ int succ_w(int x) const { return arrays() ? ar.succ(x) : sg.succ_w(x); }
   __device__ __forceinline__ int pred(int x) const { return arrays() ? ar.pred(x) : sg.pred(x); }
   __device__ __forceinline__ int adj(int x, bool up) const { return arrays() ? ar.adj(x, up) : sg.adj(x, up); }
   __device__ __forceinline__ void nbrs(int x, int& p, int& s) const {
