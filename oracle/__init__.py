@@ -25,7 +25,7 @@ _lib = None
 
 NSTATS = 16
 ST_ACO_STEPS, ST_NEW_EDGES, ST_BACKUP, ST_GLOBAL, ST_CHECKLIST, ST_POPS = 0, 1, 2, 3, 4, 5
-ST_MOVES_2OPT, ST_MOVES_OR, ST_FLIP_ELEMS, ST_VERIFY_ROUNDS = 6, 7, 8, 9
+ST_MOVES_2OPT, ST_MOVES_OR, ST_FLIP_ELEMS, ST_VERIFY_ROUNDS, ST_MOVES_3OPT = 6, 7, 8, 9, 10
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +56,7 @@ class Params(ctypes.Structure):
         ("threads", ctypes.c_int32),
         ("keep_pre_ls", ctypes.c_int32),
         ("local_search", ctypes.c_int32),
+        ("init_3opt", ctypes.c_int32),
     ]
 
 
@@ -88,6 +89,10 @@ def lib():
             L.orc_local_search.argtypes = [_P(np.int32), ctypes.c_int32, _P(np.int32), ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, _P(np.int32), _P(np.int32),
                                            _P(np.int32), ctypes.c_int32, vp]
+            L.orc_local_search_ex.restype = ctypes.c_int64
+            L.orc_local_search_ex.argtypes = [_P(np.int32), ctypes.c_int32, _P(np.int32), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(np.int32),
+                                              _P(np.int32), _P(np.int32), ctypes.c_int32, vp]
             L.orc_nn_tour.argtypes = [_P(np.int32), ctypes.c_int32, _P(np.int32), ctypes.c_int32,
                                       _P(np.int32), ctypes.c_int32, _P(np.int32)]
             L.orc_tour_length.restype = ctypes.c_int64
@@ -191,7 +196,7 @@ def tour_length(xy: np.ndarray, route: np.ndarray) -> int:
     return int(lib().orc_tour_length(xy, route.size, route))
 
 
-def local_search(xy, cand, route, queue, oropt=1, verify=1):
+def local_search(xy, cand, route, queue, oropt=1, verify=1, three_opt=0):
     """Runs Alg 3 (+ options) on a copy of `route`; returns (route, gain, stats)."""
     xy = np.ascontiguousarray(xy, dtype=np.int32).reshape(-1)
     cand = np.ascontiguousarray(cand, dtype=np.int32)
@@ -201,8 +206,8 @@ def local_search(xy, cand, route, queue, oropt=1, verify=1):
     pos[route] = np.arange(n, dtype=np.int32)
     queue = np.ascontiguousarray(queue, dtype=np.int32)
     st = np.zeros(NSTATS, np.int64)
-    g = lib().orc_local_search(xy, n, cand, cand.shape[1], oropt, verify, route, pos, queue,
-                               queue.size, _ptr(st))
+    g = lib().orc_local_search_ex(xy, n, cand, cand.shape[1], oropt, verify, three_opt, route, pos, queue,
+                                  queue.size, _ptr(st))
     return route, int(g), st
 
 

@@ -51,7 +51,8 @@
  *     c = (1 - p^(1/n)) / ((cl_size - 1) p^(1/n)), p_best = 0.05;
  *   - initial tour: nearest neighbour from node 0 (candidate list, backup
  *     list, then global nearest), then the same local search with every
- *     node queued in tour order (the paper's extra 3-opt is not applied).
+ *     node queued in tour order; with init_3opt it also tries the 3-opt
+ *     segment exchange of or3_eval() (Sec. 4.3's "2-opt and 3-opt").
  */
 #include "faco_oracle.h"
 
@@ -155,6 +156,7 @@ void orc_params_default(orc_params* p) {
   p->threads = 1;
   p->keep_pre_ls = 0;
   p->local_search = 1;
+  p->init_3opt = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -425,9 +427,68 @@ static int64_t two_opt_eval(ls_state* S, int32_t a, int32_t mv[4]) {
   return gain;
 }
 
-int64_t orc_local_search(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
-                         int32_t oropt, int32_t verify, int32_t* route, int32_t* pos,
-                         const int32_t* queue, int32_t nqueue, int64_t* stats) {
+/* 3-opt segment exchange for the initial tour (Sec. 4.3: the initial
+ * solution is improved by 2-opt and 3-opt following Bentley; the paper
+ * gives no further detail, so the move and its search are a reading).
+ * Three tour edges (a,t2), (b,b'), (c,c') are replaced by (a,b'), (b,c'),
+ * (c,t2): walking from a towards t2, the tour is a [t2 .. b] [b' .. c] c'
+ * and becomes a [b' .. c] [t2 .. b] c' -- the two sections swap places,
+ * neither is reversed (the one reconnection of three edges that is not a
+ * 2-opt move or a reversal).  Neighbour lists with Bentley's positive
+ * partial gains: t2 = succ(a) (dir 0) or pred(a) (dir 1); b' runs over
+ * NN(a) with g1 = d(a,t2) - d(a,b') > 0, b is b''s neighbour before it in
+ * the walking direction; c' runs over NN(b) with g2 = g1 + d(b,b') -
+ * d(b,c') > 0, c is c''s neighbour before it; the move is valid when, in
+ * walking order from a, 1 <= r(b) < r(c) <= n - 2.  gain = g2 + d(c,c') -
+ * d(c,t2).  The first strictly largest gain in the order (dir, b', c')
+ * wins.  mv = {a, t2, b, b', c, c'}. */
+static int64_t or3_eval(ls_state* S, int32_t a, int32_t mv[6]) {
+  int32_t n = S->n;
+  int64_t best = 0;
+  if (n < 8) return 0;
+  for (int32_t dir = 0; dir < 2; ++dir) {
+    int32_t t2 = dir == 0 ? succ_of(S, a) : pred_of(S, a);
+    int64_t d_at2 = dist(S, a, t2);
+    for (int32_t i = 0; i < S->k; ++i) {
+      int32_t b1 = S->cand[(size_t)a * S->k + i]; /* b' */
+      int64_t g1 = d_at2 - dist(S, a, b1);
+      if (g1 <= 0) continue;
+      int32_t b = dir == 0 ? pred_of(S, b1) : succ_of(S, b1);
+      for (int32_t j = 0; j < S->k; ++j) {
+        int32_t c1 = S->cand[(size_t)b * S->k + j]; /* c' */
+        int64_t g2 = g1 + dist(S, b, b1) - dist(S, b, c1);
+        if (g2 <= 0) continue;
+        int32_t c = dir == 0 ? pred_of(S, c1) : succ_of(S, c1);
+        /* positions counted from a in the walking direction */
+        int32_t rb = dir == 0 ? S->pos[b] - S->pos[a] : S->pos[a] - S->pos[b];
+        int32_t rc = dir == 0 ? S->pos[c] - S->pos[a] : S->pos[a] - S->pos[c];
+        rb = (rb % n + n) % n;
+        rc = (rc % n + n) % n;
+        if (!(rb >= 1 && rb < rc && rc <= n - 2)) continue;
+        int64_t g = g2 + dist(S, c, c1) - dist(S, c, t2);
+        if (g > best) {
+          best = g;
+          mv[0] = a; mv[1] = t2; mv[2] = b; mv[3] = b1; mv[4] = c; mv[5] = c1;
+        }
+      }
+    }
+  }
+  return best;
+}
+
+/* The segment exchange as three edge exchanges:
+ *   {a,t2},{b,b'} -> {a,b},{t2,b'};  {a,b},{c,c'} -> {a,c},{b,c'};
+ *   {a,c},{b',t2} -> {a,b'},{c,t2}. */
+static void or3_apply(ls_state* S, const int32_t mv[6]) {
+  int32_t a = mv[0], t2 = mv[1], b = mv[2], b1 = mv[3], c = mv[4], c1 = mv[5];
+  move_2opt(S, a, t2, b, b1);
+  move_2opt(S, a, b, c, c1);
+  move_2opt(S, a, c, b1, t2);
+}
+
+int64_t orc_local_search_ex(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
+                            int32_t oropt, int32_t verify, int32_t three_opt, int32_t* route,
+                            int32_t* pos, const int32_t* queue, int32_t nqueue, int64_t* stats) {
   ls_state S;
   memset(&S, 0, sizeof S);
   S.xy = xy; S.n = n; S.cand = cand; S.k = k; S.route = route; S.pos = pos; S.st = stats;
@@ -464,6 +525,18 @@ int64_t orc_local_search(const int32_t* xy, int32_t n, const int32_t* cand, int3
           changes++;
           moves_in_round++;
           if (stats) stats[ORC_ST_MOVES_OR]++;
+          continue;
+        }
+      }
+      if (three_opt) {
+        g = or3_eval(&S, a, mv);
+        if (g > 0) {
+          or3_apply(&S, mv);
+          for (int t = 0; t < 6; ++t) q_push(&S, mv[t]);
+          total_gain += g;
+          changes++;
+          moves_in_round++;
+          if (stats) stats[ORC_ST_MOVES_3OPT]++;
         }
       }
     }
@@ -485,6 +558,12 @@ int64_t orc_local_search(const int32_t* xy, int32_t n, const int32_t* cand, int3
   free(S.q);
   free(S.log);
   return total_gain;
+}
+
+int64_t orc_local_search(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
+                         int32_t oropt, int32_t verify, int32_t* route, int32_t* pos,
+                         const int32_t* queue, int32_t nqueue, int64_t* stats) {
+  return orc_local_search_ex(xy, n, cand, k, oropt, verify, 0, route, pos, queue, nqueue, stats);
 }
 
 /* ------------------------------------------------------------------ */
@@ -700,8 +779,8 @@ int orc_create(const int32_t* xy, int32_t n, int32_t k, const orc_params* p, orc
   orc_nn_tour(C->xy, n, C->cand, C->k, C->backup, C->bl, C->init_route);
   set_positions(n, C->init_route, pos);
   for (int32_t i = 0; i < n; ++i) rows[i] = C->init_route[i];
-  orc_local_search(C->xy, n, C->cand, C->k, prm.oropt, prm.verify_pass, C->init_route, pos, rows,
-                   n, NULL);
+  orc_local_search_ex(C->xy, n, C->cand, C->k, prm.oropt, prm.verify_pass, prm.init_3opt, C->init_route,
+                      pos, rows, n, NULL);
   free(rows);
   free(pos);
   C->init_len = orc_tour_length(C->xy, n, C->init_route);

@@ -33,6 +33,9 @@ typedef struct {
   int32_t local_search;   /* 1: each new tour gets the local search (FACO+LS); */
                           /* 0: base FACO, the tour is kept as constructed     */
                           /* (the study of min_new_edges, Figs. 1 and 3)       */
+  int32_t init_3opt;      /* 1: the initial tour's local search also tries     */
+                          /* 3-opt segment exchanges (Sec. 4.3; see            */
+                          /* orc_local_search_ex)                              */
 } orc_params;
 
 typedef struct orc_colony orc_colony;
@@ -51,6 +54,7 @@ enum {
   ORC_ST_MOVES_OR,        /* applied Or-opt moves                           */
   ORC_ST_FLIP_ELEMS,      /* total elements moved by reversals              */
   ORC_ST_VERIFY_ROUNDS,   /* verify rounds started                          */
+  ORC_ST_MOVES_3OPT,      /* applied 3-opt segment exchanges                */
   ORC_NSTATS = 16
 };
 
@@ -77,6 +81,12 @@ int32_t orc_roulette(const float* w, int32_t width, float u01);
 int64_t orc_local_search(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
                          int32_t oropt, int32_t verify, int32_t* route, int32_t* pos,
                          const int32_t* queue, int32_t nqueue, int64_t* stats);
+/* orc_local_search with, when three_opt = 1, a third move type tried from a
+ * node whose 2-opt and Or-opt scans found nothing: the 3-opt segment
+ * exchange (see or3_eval in the source). */
+int64_t orc_local_search_ex(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
+                            int32_t oropt, int32_t verify, int32_t three_opt, int32_t* route,
+                            int32_t* pos, const int32_t* queue, int32_t nqueue, int64_t* stats);
 
 void orc_nn_tour(const int32_t* xy, int32_t n, const int32_t* cand, int32_t k,
                  const int32_t* backup, int32_t bl, int32_t* route);

@@ -398,3 +398,87 @@ def test_source_choice_extremes(p_src, want):
     for it, h, alh, tours, lens, src, src_len, best, best_len in rows:
         assert h[3] == want
         np.testing.assert_array_equal(src, best if want else tours[int(np.argmin(lens))])
+
+
+# ---- the initial tour's 3-opt segment exchange (Sec. 4.3) --------------------
+
+def best_exchange_delta(D, route, min_seg=2):
+    """Smallest length change over every exchange of two adjacent tour
+    sections (X Y Z -> X Z Y, no reversal) whose three sections each hold
+    at least `min_seg` nodes, by explicit tour surgery."""
+    n = len(route)
+    L0 = length(D, route)
+    best = 0
+    r = list(route)
+    for i in range(n):
+        rot = r[i:] + r[:i]  # X starts at position 0
+        for j in range(min_seg, n):  # X = rot[:j]
+            for k in range(j + min_seg, n - min_seg + 1):  # Y = rot[j:k], Z = rot[k:]
+                t = rot[:j] + rot[k:] + rot[j:k]
+                best = min(best, length(D, t) - L0)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_three_opt_search_reaches_exchange_optimum(seed):
+    """With full neighbour lists, the local search with the segment exchange
+    ends in a tour that no 2-opt move, no Or-opt move and no exchange of two
+    adjacent sections (each section of >= 2 nodes) improves, checked by
+    exhaustive tour surgery; the returned gain is the length difference."""
+    n = 16 + 2 * seed
+    xy = inputs.uniform(n, seed=700 + seed, side=10000)
+    D = dmat(xy)
+    cand = oracle.knn_rows(xy, n - 1)
+    route = oracle.nn_tour(xy, cand[:, :3], cand[:, 3:6])
+    L0 = length(D, route)
+    out, gain, st = oracle.local_search(xy, cand, route, route.copy(), oropt=1, verify=1, three_opt=1)
+    assert st[oracle.ST_MOVES_2OPT] + st[oracle.ST_MOVES_OR] + st[oracle.ST_MOVES_3OPT] < n
+    assert is_perm(out, n)
+    assert length(D, out) == L0 - gain
+    assert best_2opt_delta(D, list(out)) == 0
+    assert best_oropt_delta(D, list(out)) == 0
+    assert best_exchange_delta(D, list(out)) == 0
+
+
+def test_three_opt_moves_occur_and_only_shorten():
+    """On 2-opt + Or-opt local optima of larger instances the exchange still
+    finds moves; each search only shortens the tour, and without the flag
+    the search is the plain one."""
+    found = 0
+    for seed in range(8):
+        n = 60
+        xy = inputs.uniform(n, seed=800 + seed, side=10000)
+        D = dmat(xy)
+        cand = oracle.knn_rows(xy, 8)
+        route = oracle.nn_tour(xy, cand[:, :3], cand[:, 3:6])
+        base, g0, _ = oracle.local_search(xy, cand, route, route.copy(), oropt=1, verify=1, three_opt=0)
+        plain, gp, _ = oracle.local_search(xy, cand, route, route.copy(), oropt=1, verify=1)
+        np.testing.assert_array_equal(base, plain)
+        assert g0 == gp
+        out, g1, st = oracle.local_search(xy, cand, base, base.copy(), oropt=1, verify=1, three_opt=1)
+        assert is_perm(out, n) and g1 >= 0
+        assert length(D, out) == length(D, base) - g1
+        found += int(st[oracle.ST_MOVES_3OPT])
+    assert found > 0
+
+
+def test_initial_tour_with_three_opt():
+    """The colony's initial tour with init_3opt: a permutation whose length
+    is the recomputed one (the search takes another path than without the
+    flag, so neither local optimum bounds the other), and exchange-optimal
+    for full neighbour lists on a small instance."""
+    moved = 0
+    for n, seed in ((300, 3), (500, 4)):
+        xy = inputs.uniform(n, seed=seed)
+        a = oracle.Colony(xy, 16)
+        b = oracle.Colony(xy, 16, init_3opt=1)
+        ra, La = a.initial()
+        rb, Lb = b.initial()
+        assert is_perm(rb, n) and Lb == oracle.tour_length(xy, rb)
+        moved += int(La != Lb)
+    assert moved > 0
+    xy = inputs.uniform(22, seed=41, side=5000)
+    c = oracle.Colony(xy, 21, init_3opt=1, bl_size=0)
+    r, L = c.initial()
+    D = dmat(xy)
+    assert best_2opt_delta(D, list(r)) == 0 and best_exchange_delta(D, list(r)) == 0
