@@ -71,6 +71,9 @@ typedef struct {
                           /* (the min_new_edges study, Figs. 1 and 3, uses it    */
                           /* with rho = 0.9); the initial tour's local search is */
                           /* part of the set-up either way                       */
+  int32_t init_3opt;      /* 1: the initial tour's local search (Alg 2 set-up)   */
+                          /* also tries 3-opt segment exchanges after 2-opt and  */
+                          /* Or-opt (Sec. 4.3, "2-opt and 3-opt"); default 0     */
   void* stream;           /* cudaStream_t to enqueue on (NULL = own stream)       */
 } faco_params;
 

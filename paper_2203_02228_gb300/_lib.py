@@ -39,6 +39,7 @@ class faco_params(ctypes.Structure):
         ("keep_pre_ls", ctypes.c_int32),
         ("seg_cap", ctypes.c_int32),
         ("local_search", ctypes.c_int32),
+        ("init_3opt", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -103,6 +103,7 @@ Colony colony_view(const faco_ctx* c) {
   C.n = c->n; C.k = c->k; C.bl = c->bl; C.kw = c->kw;
   C.seed = c->prm.seed; C.rho = c->prm.rho; C.min_new_edges = c->prm.min_new_edges;
   C.oropt = c->prm.oropt; C.verify = c->prm.verify_pass; C.ls = c->prm.local_search;
+  C.init3 = c->prm.init_3opt;
   C.c_min = c->c_min; C.p_src_gb = c->prm.p_source_gb;
   C.xy = c->xy; C.cand = c->cand; C.backup = c->backup; C.eta = c->eta; C.tau = c->tau;
   C.src_route = c->src_route; C.src_pos = c->src_pos; C.gb_route = c->gb_route; C.gb_pos = c->gb_pos;
@@ -292,8 +293,8 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     if (e == cudaSuccess) e = launch_positions(c->init_route, c->src_pos, n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fl, 0, n, s);
     if (e == cudaSuccess)
-      e = launch_init_ls(c->xy, n, c->cand, c->dcand, c->k, prm.oropt, prm.verify_pass, c->init_route,
-                         c->src_pos, q, fl, lg, s);
+      e = launch_init_ls(c->xy, n, c->cand, c->dcand, c->k, prm.oropt, prm.verify_pass, prm.init_3opt,
+                         c->init_route, c->src_pos, q, fl, lg, s);
     if (e == cudaSuccess) e = launch_tour_length(c->xy, c->init_route, n, c->len_tmp, s);
     Colony C = colony_view(c);
     if (e == cudaSuccess) e = launch_state_init(C, c->len_tmp, s);
@@ -464,6 +465,7 @@ int faco_params_default(faco_params* p) {
   p->keep_pre_ls = 0;
   p->seg_cap = -1;
   p->local_search = 1;
+  p->init_3opt = 0;
   p->stream = nullptr;
   return FACO_OK;
 }

@@ -68,6 +68,7 @@ struct Colony {
   int32_t min_new_edges;
   int32_t oropt, verify;
   int32_t ls;            // 1: local search on every new tour; 0: base FACO
+  int32_t init3;         // 1: the initial tour's search also tries 3-opt segment exchanges
   double c_min;          // tau_min / tau_max ratio
   double p_src_gb;
   const int2* xy;        // [n] coordinates, node order

@@ -77,7 +77,7 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
                            int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
                            const int4* recs, cudaStream_t s);
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
-                           int verify, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
+                           int verify, int init3, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s);
 cudaError_t launch_init_tour_batch(const Colony* cols, const ColonySetup* sets, int count, int max_n, int stage,
                                    cudaStream_t s);

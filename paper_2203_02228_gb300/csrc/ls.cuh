@@ -335,6 +335,77 @@ __device__ __forceinline__ void eval_both(const Tour& T, int a, bool do_or, int6
   }
 }
 
+// The 3-opt segment exchange of the initial tour (Sec. 4.3: 2-opt and
+// 3-opt following Bentley; the move and its search are a reading): the
+// tour edges (a,t2), (b,b'), (c,c') become (a,b'), (b,c'), (c,t2), so that,
+// walking from a towards t2, a [t2..b] [b'..c] c' turns into
+// a [b'..c] [t2..b] c' -- two adjacent sections swap places, neither
+// reversed.  t2 is a's successor (dir 0) or predecessor (dir 1); b' runs
+// over NN(a) with g1 = d(a,t2) - d(a,b') > 0 and b is the node before b' in
+// the walking direction; c' runs over NN(b) with g2 = g1 + d(b,b') -
+// d(b,c') > 0 and c is the node before c'; valid when, counted from a in
+// the walking direction, 1 <= r(b) < r(c) <= n - 2.  gain = g2 + d(c,c') -
+// d(c,t2); the first strictly largest gain in the order (dir, b', c') wins.
+// The warp takes the (dir, b', c') combinations 32 at a time, lane = order
+// index mod 32.  Returns the gain (0: none) and mv = {a, t2, b, b', c, c'}.
+// Warp-collective; the tour's nodes and coordinates as the Tour names them.
+template <class Tour>
+__device__ __forceinline__ int64_t eval_or3(const Tour& T, int a, int mv[6]) {
+  const int n = T.n, k = T.k, lane = lane_id();
+  if (n < 8) return 0;
+  int p, s1;
+  T.nbrs(a, p, s1);
+  const int2 xa = T.coord(a), xs = T.coord(s1), xp = T.coord(p);
+  const int d_as = euc2d(xa, xs), d_ap = euc2d(xa, xp);
+  const int pa = T.pos_of(a);
+  const int kk = k * k, total = 2 * kk;
+  int32_t best = 0;
+  int bi = INT_MAX, bb = -1, bb1 = -1, bc = -1, bc1 = -1;
+  for (int idx = lane; idx < total; idx += 32) {
+    const int dir = idx >= kk ? 1 : 0;
+    const int r = idx - dir * kk;
+    const int i = r / k, j = r - i * k;
+    const int t2 = dir ? p : s1;
+    const int2 xt2 = dir ? xp : xs;
+    const int g1 = (dir ? d_ap : d_as) - T.cdist(a, i);
+    if (g1 <= 0) continue;
+    const int b1 = T.cand(a, i);
+    const int b = T.adj(b1, dir != 0);  // dir 0: pred(b'), dir 1: succ(b')
+    const int2 xb = T.coord(b), xb1 = T.coord(b1);
+    const int g2 = g1 + euc2d(xb, xb1) - T.cdist(b, j);
+    if (g2 <= 0) continue;
+    const int c1 = T.cand(b, j);
+    const int c = T.adj(c1, dir != 0);
+    int rb = dir ? pa - T.pos_of(b) : T.pos_of(b) - pa;
+    int rc = dir ? pa - T.pos_of(c) : T.pos_of(c) - pa;
+    if (rb < 0) rb += n;
+    if (rc < 0) rc += n;
+    if (!(rb >= 1 && rb < rc && rc <= n - 2)) continue;
+    const int2 xc = T.coord(c), xc1 = T.coord(c1);
+    const int32_t g = g2 + euc2d(xc, xc1) - euc2d(xc, xt2);
+    if (g > best) {  // idx grows along the lane's loop: ties keep the earlier
+      best = g;
+      bi = idx;
+      bb = b;
+      bb1 = b1;
+      bc = c;
+      bc1 = c1;
+    }
+  }
+  int32_t g = best > 0 ? best : 0;
+  int32_t wi = best > 0 ? bi : INT_MAX;
+  warp_max_gain(g, wi);
+  if (g <= 0) return 0;
+  const int wl = wi & 31;
+  mv[0] = a;
+  mv[1] = wi >= kk ? p : s1;
+  mv[2] = __shfl_sync(kFull, bb, wl);
+  mv[3] = __shfl_sync(kFull, bb1, wl);
+  mv[4] = __shfl_sync(kFull, bc, wl);
+  mv[5] = __shfl_sync(kFull, bc1, wl);
+  return g;
+}
+
 // Evaluation from a on any tour; representations that can change on the
 // way (a segment table that may move to arrays) provide their own overload
 // that picks one concrete representation per call.

@@ -20,6 +20,7 @@ int check_faco_params(const faco_params& p) {
   if (p.min_new_edges < 1 || p.bl_size < 0 || p.bl_size > 128) return FACO_E_ARG;
   if (p.seg_cap < -1 || (p.seg_cap > 0 && p.seg_cap < 8) || p.seg_cap > 4096) return FACO_E_ARG;
   if (p.local_search != 0 && p.local_search != 1) return FACO_E_ARG;
+  if (p.init_3opt != 0 && p.init_3opt != 1) return FACO_E_ARG;
   return FACO_OK;
 }
 
@@ -144,6 +145,7 @@ void group_layout(Group& g, char* base) {
     c.oropt = g.prm.oropt;
     c.verify = g.prm.verify_pass;
     c.ls = g.prm.local_search;
+    c.init3 = g.prm.init_3opt;
     const double pr = std::pow(g.prm.p_best, 1.0 / (double)n);
     c.c_min = (1.0 - pr) / ((double)(c.k - 1) * pr);
     c.p_src_gb = g.prm.p_source_gb;

@@ -251,10 +251,11 @@ __device__ __forceinline__ bool in_span(int p, int2 sp, int n) {
 constexpr int kWin = 32;
 
 template <class TT>
-__device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32_t* queue, uint8_t* flags,
+__device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int init3, int32_t* queue, uint8_t* flags,
                                              int32_t* logb) {
   __shared__ int64_t s_gain[kWin];
   __shared__ int s_mv[kWin][8];
+  __shared__ int s_any[kWin];             // 1: the evaluation read beyond s_dep (3-opt scan): any move drops it
   __shared__ int s_node[kWin];            // node whose evaluation the slot holds, -1: none
   __shared__ int s_dep[kWin][kMaxK + 1];  // [0]: its position, [1 + s]: candidate s's position
   __shared__ SpanLog s_log;
@@ -313,9 +314,13 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
       const int my_node = __shfl_sync(kFull, node, w & 31);
       const int my_slot = (base + w) & (kWin - 1);
       if (w < R && ((bmiss >> w) & 1u)) {
-        int mv2[4], mvo[7];
-        int64_t g2, go;
+        int mv2[4], mvo[7], mv3[6];
+        int64_t g2, go, g3 = 0;
         eval_both(T, my_node, oropt != 0, g2, mv2, go, mvo);
+        // the 3-opt exchange only when neither 2-opt nor Or-opt improves
+        // (g2, go are the warp's reductions: the branch is warp-uniform)
+        const bool try3 = init3 && !(g2 > 0) && !(go > 0);
+        if (try3) g3 = eval_or3(T, my_node, mv3);
         if (lane < k) s_dep[my_slot][1 + lane] = T.pos_of(T.cand(my_node, lane));
         if (lane == 0) {
           s_dep[my_slot][0] = T.pos_of(my_node);
@@ -323,11 +328,16 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
             s_gain[my_slot] = g2;
             for (int t = 0; t < 4; ++t) s_mv[my_slot][t] = mv2[t];
             s_mv[my_slot][7] = 0;
+          } else if (g3 > 0) {
+            s_gain[my_slot] = g3;
+            for (int t = 0; t < 6; ++t) s_mv[my_slot][t] = mv3[t];
+            s_mv[my_slot][7] = 2;
           } else {
             s_gain[my_slot] = go > 0 ? go : 0;
             for (int t = 0; t < 7; ++t) s_mv[my_slot][t] = mvo[t];
             s_mv[my_slot][7] = 1;
           }
+          s_any[my_slot] = try3 ? 1 : 0;
           s_node[my_slot] = my_node;
         }
       }
@@ -370,17 +380,21 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
       if (tid == 0) s_node[win] = -1;
       if (mv[7] == 0) {
         cta_flip(T, mv[1], mv[2], s_log);
-      } else {
+      } else if (mv[7] == 1) {
         cta_move2(T, mv[0], mv[1], mv[4], mv[5], s_log);
         cta_move2(T, mv[0], mv[4], mv[3], mv[2], s_log);
         if (mv[6]) cta_move2(T, mv[4], mv[2], mv[1], mv[5], s_log);
+      } else {  // 3-opt exchange {a, t2, b, b', c, c'} as three edge exchanges
+        cta_move2(T, mv[0], mv[1], mv[2], mv[3], s_log);  // {a,t2},{b,b'} -> {a,b},{t2,b'}
+        cta_move2(T, mv[0], mv[2], mv[4], mv[5], s_log);  // {a,b},{c,c'} -> {a,c},{b,c'}
+        cta_move2(T, mv[0], mv[4], mv[3], mv[1], s_log);  // {a,c},{b',t2} -> {a,b'},{c,t2}
       }
       // drop the evaluations that read a reversed position (warp w checks slot w)
       {
         const int sn = s_node[w];
         if (sn >= 0) {
           const int ns = s_log.count;
-          bool hit = false;
+          bool hit = s_any[w] != 0;
           if (lane < k) {
             const int tb = s_dep[w][1 + lane];
             for (int q = 0; q < ns && !hit; ++q) {
@@ -389,7 +403,7 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
                     in_span(tb + 1 == n ? 0 : tb + 1, sp, n);
             }
           }
-          if (lane == 31) {
+          if (lane == 31 && !hit) {
             const int t0 = s_dep[w][0];
             for (int q = 0; q < ns && !hit; ++q) {
               const int2 sp = s_log.span[q];
@@ -405,7 +419,7 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
         }
       }
       if (w == 0) {
-        const int qn2 = ls_push_warp(E, mv, mv[7] == 0 ? 4 : 6, s_qh, s_qn);
+        const int qn2 = ls_push_warp(E, mv, mv[7] == 0 ? 4 : 6, s_qh, s_qn);  // 2-opt: 4 ends, else 6
         if (lane == 0) {
           s_qn = qn2;
           s_changes++;
@@ -430,27 +444,27 @@ __device__ __forceinline__ void init_ls_body(TT& T, int oropt, int verify, int32
 // the search works on `pos` in global memory.
 template <bool SP>
 __device__ __forceinline__ void init_ls_run(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k,
-                                            int oropt, int verify, int32_t* route, int32_t* pos, int32_t* queue,
-                                            uint8_t* flags, int32_t* logb) {
+                                            int oropt, int verify, int init3, int32_t* route, int32_t* pos,
+                                            int32_t* queue, uint8_t* flags, int32_t* logb) {
   if constexpr (SP) {
     extern __shared__ __align__(16) unsigned char s_pos[];
     SmemPosTour T = smem_pos_tour(s_pos, n, k, route, xy, cand, dcand);
     smem_pos_load(T);
-    init_ls_body(T, oropt, verify, queue, flags, logb);
+    init_ls_body(T, oropt, verify, init3, queue, flags, logb);
     __syncthreads();
     for (int x = threadIdx.x; x < n; x += blockDim.x) pos[x] = T.pos_of(x);
   } else {
     ArrTour T{n, k, route, pos, xy, cand, k, dcand};
-    init_ls_body(T, oropt, verify, queue, flags, logb);
+    init_ls_body(T, oropt, verify, init3, queue, flags, logb);
   }
 }
 
 template <bool SP>
 __global__ void __launch_bounds__(1024) k_init_ls(const int2* xy, int n, const int32_t* cand,
-                                                  const int32_t* dcand, int k, int oropt, int verify,
+                                                  const int32_t* dcand, int k, int oropt, int verify, int init3,
                                                   int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                                                   int32_t* logb) {
-  init_ls_run<SP>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+  init_ls_run<SP>(xy, n, cand, dcand, k, oropt, verify, init3, route, pos, queue, flags, logb);
 }
 
 // Batch: one block per colony; positions of the initial tour in src_pos.
@@ -458,7 +472,7 @@ template <bool SP>
 __global__ void __launch_bounds__(1024) k_init_ls_b(const Colony* cols, const ColonySetup* sets) {
   const Colony C = cols[blockIdx.x];
   const ColonySetup S = sets[blockIdx.x];
-  init_ls_run<SP>(C.xy, C.n, S.cand, S.dcand, C.k, C.oropt, C.verify, S.init_route, C.src_pos, S.queue, S.flags,
+  init_ls_run<SP>(C.xy, C.n, S.cand, S.dcand, C.k, C.oropt, C.verify, C.init3, S.init_route, C.src_pos, S.queue, S.flags,
                   S.logb);
 }
 
@@ -516,13 +530,13 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
 }
 
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
-                           int verify, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
+                           int verify, int init3, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s) {
   const size_t sm = init_ls_pos_smem(reinterpret_cast<const void*>(k_init_ls<true>), n);
   if (sm > 0)
-    k_init_ls<true><<<1, 1024, sm, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+    k_init_ls<true><<<1, 1024, sm, s>>>(xy, n, cand, dcand, k, oropt, verify, init3, route, pos, queue, flags, logb);
   else
-    k_init_ls<false><<<1, 1024, 0, s>>>(xy, n, cand, dcand, k, oropt, verify, route, pos, queue, flags, logb);
+    k_init_ls<false><<<1, 1024, 0, s>>>(xy, n, cand, dcand, k, oropt, verify, init3, route, pos, queue, flags, logb);
   return cudaGetLastError();
 }
 

@@ -43,8 +43,8 @@ def test_params_struct_matches_defaults(lib):
     p = params_default()
     assert p.seed == 1 and p.rho == np.float32(0.5) and p.min_new_edges == 8 and p.bl_size == 64
     assert p.p_best == 0.05 and p.p_source_gb == 0.01 and p.oropt == 1 and p.verify_pass == 1
-    assert p.seg_cap == -1 and p.local_search == 1
-    assert ctypes.sizeof(faco_params) == 72  # the C layout of include/faco.h on LP64
+    assert p.seg_cap == -1 and p.local_search == 1 and p.init_3opt == 0
+    assert ctypes.sizeof(faco_params) == 80  # the C layout of include/faco.h on LP64
 
 
 def test_invalid_arguments_are_rejected(lib):

@@ -174,3 +174,19 @@ def test_initial_search_with_positions_in_global_memory():
         assert lens[i] == L, i
         np.testing.assert_array_equal(tours[i], t)
         assert b.stats(i).initial_length == c.stats().initial_length
+
+
+def test_batch_initial_tours_with_three_opt():
+    """Batched set-up with init_3opt: every colony's initial tour equals the
+    oracle's (one block per colony, the same search)."""
+    xs = mixed_instances()
+    seeds = np.arange(11, 11 + len(xs), dtype=np.uint64)
+    b = Batch(xs, 16, seeds=seeds, init_3opt=1)
+    b.iterate(8, 2)
+    for i, xy in enumerate(xs):
+        o = oracle.Colony(xy, 16, seed=int(seeds[i]), init_3opt=1, threads=4)
+        o.iterate(8, 2)
+        t, L = b.best(i)
+        assert L == o.best()[1]
+        np.testing.assert_array_equal(t, o.best()[0])
+        assert b.stats(i).initial_length == o.initial()[1]

@@ -295,3 +295,42 @@ def test_one_colony_above_shared_position_limit():
     np.testing.assert_array_equal(g.ant_tours()[1], oal[0])
     np.testing.assert_array_equal(g.history()[-1], oh[0])
     assert_same_state(g, o, 256)
+
+
+# ---- the initial tour with 3-opt segment exchanges (init_3opt) --------------
+
+@pytest.mark.parametrize("kind", ["uniform", "stippled", "lattice", "tiny"])
+def test_initial_tour_with_three_opt(kind):
+    """init_3opt = 1: the initial tour's search also tries the 3-opt
+    segment exchange (Sec. 4.3); the tour, its length and the first
+    iterations equal the oracle's."""
+    if kind == "uniform":
+        xy = inputs.uniform(2500, seed=15)
+    elif kind == "stippled":
+        xy = inputs.stippled(3000, seed=16, blobs=10, ridges=2, side=60_000)
+    elif kind == "lattice":
+        xy = inputs.lattice(30, 40, step=5)
+    else:
+        xy = inputs.uniform(12, seed=17, side=1000)
+    g = Colony(xy, 16, init_3opt=1, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, init_3opt=1, threads=8)
+    gi, gL = g.initial()
+    oi, oL = o.initial()
+    assert gL == oL
+    np.testing.assert_array_equal(gi, oi)
+    plain = oracle.Colony(xy, 16, threads=8)
+    if kind in ("uniform", "stippled"):
+        assert plain.initial()[1] != oL  # the exchange changed the search's path
+    g.iterate(16, 3)
+    oh, _ = o.iterate(16, 3)
+    np.testing.assert_array_equal(g.history(), oh)
+    assert_same_state(g, o, 16)
+
+
+def test_initial_tour_with_three_opt_above_shared_position_limit():
+    """The same with tour positions in global memory (n = 110,000)."""
+    xy = inputs.stippled(110_000, seed=1313, blobs=40, ridges=5, side=100_000)
+    g = Colony(xy, 16, init_3opt=1)
+    o = oracle.Colony(xy, 16, init_3opt=1, threads=16)
+    assert g.initial()[1] == o.initial()[1]
+    np.testing.assert_array_equal(g.initial()[0], o.initial()[0])
