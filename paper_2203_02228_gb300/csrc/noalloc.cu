@@ -28,7 +28,9 @@ constexpr int64_t kScratchInts = 8 + kNoAllocMaxCells + (kNoAllocMaxCells + 1) +
 
 __device__ __align__(256) int32_t g_list_scratch[kScratchInts];
 
-// Device address of g_list_scratch per device, looked up on first use.
+// Device address of g_list_scratch per device, looked up on first use and
+// kept for the life of the process (a cudaDeviceReset would invalidate it;
+// the header says the call is not to be used across one).
 constexpr int kMaxDevices = 64;
 int32_t* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
