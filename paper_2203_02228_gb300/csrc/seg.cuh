@@ -485,24 +485,28 @@ struct SegTour {
     const int ri = bsearch_le_warp(T.offA, S, i);
     const int rj = (j1 == 0) ? S - 1 : bsearch_le_warp(T.offA, S, j1) - 1;
     if (i <= j) {
-      // contiguous ranks ri..rj: new off = i + j + 1 - off - len, direction flips
-      const int c = rj - ri + 1;
-      for (int m = lane; m < c; m += 32) {
-        Seg& s = T.sg[T.A[ri + m]];
-        s.off = i + j + 1 - s.off - s.len;
-        s.rev ^= 1;
-      }
-      __syncwarp();
-      for (int m = lane; m < c / 2; m += 32) {
-        const uint16_t a = T.A[ri + m], b = T.A[rj - m];
-        T.A[ri + m] = b;
-        T.A[rj - m] = a;
-      }
-      __syncwarp();
-      for (int m = lane; m < c; m += 32) {  // keys of the reversed ranks
-        const int id = T.A[ri + m];
-        T.offA[ri + m] = T.sg[id].off;
-        T.rankA[id] = (uint16_t)(ri + m);
+      // contiguous ranks ri..rj: new off = i + j + 1 - off - len, direction
+      // flips, and the ranks reverse.  Lane m takes the pair of ranks
+      // (ri + m, rj - m) in one pass: the pairs, their ids and their
+      // segments are disjoint, so no lane reads what another writes.
+      const int c = rj - ri + 1, h = (c + 1) >> 1;
+      for (int m = lane; m < h; m += 32) {
+        const int ra = ri + m, rb = rj - m;
+        const int ida = T.A[ra], idb = T.A[rb];
+        const Seg sa = T.sg[ida], sb = T.sg[idb];
+        const int offa = i + j + 1 - sa.off - sa.len, offb = i + j + 1 - sb.off - sb.len;
+        T.sg[ida].off = offa;
+        T.sg[ida].rev = sa.rev ^ 1;
+        T.A[rb] = (uint16_t)ida;
+        T.offA[rb] = offa;
+        T.rankA[ida] = (uint16_t)rb;
+        if (rb != ra) {
+          T.sg[idb].off = offb;
+          T.sg[idb].rev = sb.rev ^ 1;
+          T.A[ra] = (uint16_t)idb;
+          T.offA[ra] = offb;
+          T.rankA[idb] = (uint16_t)ra;
+        }
       }
       __syncwarp();
       seg_merge_at(T, rj);      // the span's right end and its old right neighbour
