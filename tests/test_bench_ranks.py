@@ -70,3 +70,41 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(Args(), {"ants": 1024, "iters": 100, "n": 100_000})
     assert buf.getvalue() == ""
+
+
+def test_plain_loop_times_follow_first_come_first_served():
+    """The plain loop serves one request at a time in arrival order:
+    completion C_i = max(A_i, C_{i-1}) + S_i (checked by an explicit event
+    simulation of a single server)."""
+    import numpy as np
+
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        m = int(rng.integers(1, 40))
+        arr = np.cumsum(rng.exponential(0.3, m))
+        svc = rng.uniform(0.05, 0.8, m)
+        got = bench.plain_loop_times(arr, svc)
+        t, busy_until = 0.0, 0.0
+        want = []
+        for a_i, s_i in zip(arr, svc):  # the server idles until the next arrival
+            t = a_i if a_i > busy_until else busy_until
+            busy_until = t + s_i
+            want.append(busy_until)
+        np.testing.assert_allclose(got, want)
+        assert np.all(got - arr >= svc - 1e-12)
+
+
+def test_serve_plan_caps_the_lowest_rates():
+    plan = dict(bench.serve_plan([1, 2, 5, 10, 200], 100))
+    assert plan[1] == 30 and plan[2] == 60 and plan[5] == 100 and plan[10] == 100 and plan[200] == 100
+    assert dict(bench.serve_plan([0.5], 100))[0.5] == 30
+
+
+def test_roofline_line_rates():
+    r = bench.roofline_line("k", 100, 4, 10, ants_ms=20.0, ants_launches=10, algo_bytes=10 * 6e9, peak=6000.0,
+                            peak_src="measured", l2_peak=12000.0, traffic=(1e8, 5e9))
+    assert abs(r["avg_launch_ms"] - 2.0) < 1e-12
+    assert abs(r["achieved"] - 3000.0) < 1e-9 and abs(r["frac"] - 0.5) < 1e-12
+    assert abs(r["dram_gbs"] - 50.0) < 1e-9 and abs(r["l2_gbs"] - 2500.0) < 1e-9
+    assert abs(r["l2_frac"] - 2500.0 / 12000.0) < 1e-12
+    assert bench.roofline_line("k", 1, 1, 1, 0.0, 0, 0, 1.0, "m", None) is None
