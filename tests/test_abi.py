@@ -146,3 +146,27 @@ def test_server_without_gpu_and_request_sizes(lib):
     if not torch.cuda.is_available():
         h = ctypes.c_void_p()
         assert lib.faco_server_create(1 << 20, None, ctypes.byref(h)) == _lib.FACO_E_CUDA
+
+
+def test_diagnostic_calls_reject_bad_arguments(lib):
+    """The L2 probe and the tuner report check their arguments before any
+    device work."""
+    g = ctypes.c_double()
+    assert lib.faco_l2_probe(1 << 10, 10, ctypes.byref(g)) == _lib.FACO_E_ARG  # below 1 MiB
+    assert lib.faco_l2_probe(48 << 20, 0, ctypes.byref(g)) == _lib.FACO_E_ARG  # no repetitions
+    assert lib.faco_l2_probe(48 << 20, 10, None) == _lib.FACO_E_ARG
+    cnt = ctypes.c_int32()
+    assert lib.faco_batch_tuner_report(None, 4, ctypes.byref(cnt)) == _lib.FACO_E_ARG
+    assert lib.faco_batch_tuner_report(None, 0, None) == _lib.FACO_E_ARG
+    assert lib.faco_batch_tuner_report(None, 0, ctypes.byref(cnt)) == _lib.FACO_OK
+    assert cnt.value == 0  # nothing tuned in this process (no GPU here)
+
+
+def test_init_3opt_is_validated(lib):
+    xy = np.zeros((10, 2), np.int32)
+    xy[:, 0] = np.arange(10)
+    p = params_default()
+    p.init_3opt = 2
+    h = ctypes.c_void_p()
+    assert lib.faco_create_ex(xy.ctypes.data_as(ctypes.c_void_p), 10, 4, ctypes.byref(p),
+                              ctypes.byref(h)) == _lib.FACO_E_ARG
