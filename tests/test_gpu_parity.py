@@ -334,3 +334,21 @@ def test_initial_tour_with_three_opt_above_shared_position_limit():
     o = oracle.Colony(xy, 16, init_3opt=1, threads=16)
     assert g.initial()[1] == o.initial()[1]
     np.testing.assert_array_equal(g.initial()[0], o.initial()[0])
+
+
+def test_stippled100k_steady_state():
+    """The n = 100,000 workload past its first iterations (24 iterations of
+    1,024 ants): the source has moved off the initial tour, searches run
+    thousands of pops and the construction's nearest-unvisited searches
+    take the block-wide path -- the whole history, every ant's length in
+    the last iteration, and the final state equal the oracle's."""
+    xy = inputs.workload_points("stippled100k")
+    g = Colony(xy, 16, keep_ant_tours=1)
+    o = oracle.Colony(xy, 16, threads=16)
+    g.iterate(1024, 24)
+    oh, oal = o.iterate(1024, 24)
+    np.testing.assert_array_equal(g.history(), oh)
+    np.testing.assert_array_equal(g.ant_tours()[1], oal[-1])
+    assert_same_state(g, o, 1024)
+    st = g.stats()
+    assert st.global_picks > 0 and st.moves_or > 0
