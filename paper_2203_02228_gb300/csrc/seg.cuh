@@ -9,9 +9,11 @@
 // source.  Nodes are named by their source position.  Two orders index the
 // table: A (ids by ant position, A[0] at position 0) and B (ids by lo).
 // Segments never straddle ant position 0 nor the source's end, so every
-// lookup is a binary search.  A reversal of ant positions i..j splits the
-// segments at i and j+1, reverses that part of A and flips each segment's
-// direction -- exactly the array reversal, entry for entry, in O(segments).
+// lookup is a binary search; the inverse orders (rankA, rankB: the rank of
+// each id) make every lookup by id direct.  A reversal of ant positions
+// i..j splits the segments at i and j+1, reverses that part of A and flips
+// each segment's direction -- exactly the array reversal, entry for entry,
+// in O(segments).
 // Neighbouring segments that continue each other are merged back.  When the
 // table is full the operation reports failure and the caller redoes the ant
 // with explicit arrays (same result, more memory traffic).
@@ -35,13 +37,15 @@ struct SegTab {
   int32_t* loB;      // [cap] sg[B[r]].lo
   uint16_t* tmp;     // [2 * cap + 2] scratch
   uint16_t* rankA;   // [cap] rank in A of each id
+  uint16_t* rankB;   // [cap] rank in B of each id
   int32_t* S;        // segment count (shared)
   int cap;
 };
 
-// bytes of shared memory per warp for a table of `cap` segments
+// bytes of shared memory per segment, and per table of `cap` segments
+constexpr size_t kSegBytes = sizeof(Seg) + 6 * sizeof(uint16_t) + 2 * sizeof(int32_t);
 __host__ __device__ constexpr size_t segtab_bytes(int cap) {
-  return (size_t)cap * (sizeof(Seg) + 5 * sizeof(uint16_t) + 2 * sizeof(int32_t)) + 2 * sizeof(uint16_t) + 16;
+  return (size_t)cap * kSegBytes + 2 * sizeof(uint16_t) + 16;
 }
 
 __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
@@ -60,7 +64,9 @@ __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
   p += (size_t)(2 * cap + 2) * sizeof(uint16_t);
   T.rankA = reinterpret_cast<uint16_t*>(p);
   p += (size_t)cap * sizeof(uint16_t);
-  T.S =reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+  T.rankB = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * sizeof(uint16_t);
+  T.S = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
   T.cap = cap;
   return T;
 }
@@ -69,7 +75,7 @@ __device__ __forceinline__ SegTab segtab_at(char* base, int cap) {
 // segments are free (the local search does not need them): the same
 // shared memory, whole multiples of 32 segments added.
 __host__ __device__ constexpr int segtab_cap_ls(size_t vis_bytes, int cap) {
-  return cap + (int)((vis_bytes / (sizeof(Seg) + 5 * sizeof(uint16_t) + 2 * sizeof(int32_t))) & ~(size_t)31);
+  return cap + (int)((vis_bytes / kSegBytes) & ~(size_t)31);
 }
 
 // Moves the table `from` (placed after the visited bits) to `to` (placed at
@@ -106,17 +112,19 @@ __device__ __forceinline__ void seg_relayout(const SegTab& from, const SegTab& t
   }
   for (int c = 0; c < S; c += T) {
     const int r = c + t;
-    uint16_t a = 0, b = 0, k = 0;
+    uint16_t a = 0, b = 0, k = 0, kb = 0;
     if (r < S) {
       a = from.A[r];
       b = from.B[r];
       k = from.rankA[r];
+      kb = from.rankB[r];
     }
     __syncthreads();
     if (r < S) {
       to.A[r] = a;
       to.B[r] = b;
       to.rankA[r] = k;
+      to.rankB[r] = kb;
     }
     __syncthreads();
   }
@@ -170,26 +178,23 @@ __device__ __forceinline__ void u16_insert(uint16_t* arr, int S, int r, uint16_t
   __syncwarp();
 }
 
-// Rebuild the search keys from the orders (warp-collective).
+// Rebuild the search keys and the inverse orders from the orders
+// (warp-collective).
 __device__ __forceinline__ void segtab_keys(const SegTab& T) {
   const int S = *T.S;
   for (int r = lane_id(); r < S; r += 32) {
-    const int ida = T.A[r];
+    const int ida = T.A[r], idb = T.B[r];
     T.offA[r] = T.sg[ida].off;
     T.rankA[ida] = (uint16_t)r;
-    T.loB[r] = T.sg[T.B[r]].lo;
+    T.loB[r] = T.sg[idb].lo;
+    T.rankB[idb] = (uint16_t)r;
   }
   __syncwarp();
 }
 
-// Rank in B of segment id (by its lo; warp-collective).
-__device__ __forceinline__ int rank_B(const SegTab& T, int id) {
-  return bsearch_le_warp(T.loB, *T.S, T.sg[id].lo);
-}
-
 // The two inserts of a split in one pass: (idA, keyA) at index rA of
-// A/offA (rankA follows) and (idB, keyB) at index rB of B/loB, both
-// arrays of S entries (warp-collective).
+// A/offA and (idB, keyB) at index rB of B/loB, both arrays of S entries;
+// rankA and rankB follow (warp-collective).
 __device__ __forceinline__ void ins2_both(const SegTab& T, int S, int rA, int idA, int32_t keyA, int rB, int idB,
                                           int32_t keyB) {
   const int lane = lane_id();
@@ -215,6 +220,7 @@ __device__ __forceinline__ void ins2_both(const SegTab& T, int S, int rA, int id
     if (idx >= rB) {
       T.B[idx + 1] = vb;
       T.loB[idx + 1] = kb;
+      T.rankB[vb] = (uint16_t)(idx + 1);
     }
     __syncwarp();
   }
@@ -224,12 +230,13 @@ __device__ __forceinline__ void ins2_both(const SegTab& T, int S, int rA, int id
     T.rankA[idA] = (uint16_t)rA;
     T.B[rB] = (uint16_t)idB;
     T.loB[rB] = keyB;
+    T.rankB[idB] = (uint16_t)rB;
   }
   __syncwarp();
 }
 
-// The two removals of a merge in one pass: index rA of A/offA (rankA
-// follows) and index rB of B/loB, arrays of S entries (warp-collective).
+// The two removals of a merge in one pass: index rA of A/offA and index rB
+// of B/loB, arrays of S entries; rankA and rankB follow (warp-collective).
 __device__ __forceinline__ void del_both(const SegTab& T, int S, int rA, int rB) {
   const int lane = lane_id();
   for (int e = (rA < rB ? rA : rB) + 1; e < S; e += 32) {
@@ -254,23 +261,25 @@ __device__ __forceinline__ void del_both(const SegTab& T, int S, int rA, int rB)
     if (db) {
       T.B[idx - 1] = vb;
       T.loB[idx - 1] = kb;
+      T.rankB[vb] = (uint16_t)(idx - 1);
     }
     __syncwarp();
   }
 }
 
-// Ensure a segment starts at ant position t (0 < t < n).  Keys are current
-// on entry and on exit.  false: table full.
-static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
+// Ensure a segment starts at ant position t (0 < t < n), given the id of
+// the segment that holds t.  Keys and ranks are current on entry and on
+// exit.  Returns the id of the segment that starts at t (id itself when t
+// is already its first position, else the new id, which takes the part
+// from t on), or -1 when the table is full.
+static __device__ __noinline__ int seg_split(const SegTab& T, int t, int id) {
   const int S = *T.S;
-  const int r = bsearch_le_warp(T.offA, S, t);
-  const int id = T.A[r];
   const Seg s = T.sg[id];
-  if (s.off == t) return true;
-  if (S >= T.cap) return false;
+  if (s.off == t) return id;
+  if (S >= T.cap) return -1;
   const int d = t - s.off;
   const int nid = S;
-  const int rb = rank_B(T, id);
+  const int r = T.rankA[id], rb = T.rankB[id];
   __syncwarp();
   if (lane_id() == 0) {
     if (!s.rev) {
@@ -291,18 +300,19 @@ static __device__ __noinline__ bool seg_split(const SegTab& T, int t) {
   }
   if (lane_id() == 0) *T.S = S + 1;
   __syncwarp();
-  return true;
+  return nid;
 }
 
 // Merge ant ranks r and r+1 if the second continues the first in the
-// source (r + 1 > 0, so never across ant position 0).  Keys stay current.
+// source (r + 1 > 0, so never across ant position 0).  Keys and ranks stay
+// current.
 static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   const int S = *T.S;
   if (r < 0 || r + 1 >= S) return;
   const int ia = T.A[r], ib = T.A[r + 1];
   const Seg a = T.sg[ia], b = T.sg[ib];
   if (!(a.rev == b.rev && (a.rev ? (b.lo + b.len == a.lo) : (a.lo + a.len == b.lo)))) return;
-  const int rbb = bsearch_le_warp(T.loB, S, b.lo);
+  const int rbb = T.rankB[ib];
   __syncwarp();
   if (lane_id() == 0) {
     T.sg[ia].len = a.len + b.len;
@@ -316,14 +326,14 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   const int last = S - 1;
   if (ib != last) {
     const Seg sl = T.sg[last];
-    const int ra = T.rankA[last];
-    const int rl = bsearch_le_warp(T.loB, S - 1, sl.lo);
+    const int ra = T.rankA[last], rl = T.rankB[last];
     __syncwarp();
     if (lane_id() == 0) {
       T.sg[ib] = sl;
       T.A[ra] = (uint16_t)ib;
       T.rankA[ib] = (uint16_t)ra;
       T.B[rl] = (uint16_t)ib;
+      T.rankB[ib] = (uint16_t)rl;
     }
   }
   if (lane_id() == 0) *T.S = S - 1;
@@ -383,6 +393,36 @@ struct SegTour {
   __device__ __forceinline__ int succ_w(int q) const {
     int id = T.B[bsearch_le_warp(T.loB, *T.S, q)];
     return step_up(q, id);
+  }
+  // pos_of for two warp-uniform nodes, with the segments that hold them
+  // (warp-collective): the two searches of B go level by level together,
+  // so that their shared-memory round trips overlap.
+  __device__ __forceinline__ void pos_id2_w(int q1, int q2, int& t1, int& id1, int& t2, int& id2) const {
+    const int lane = lane_id(), S = *T.S;
+    int lo1 = 0, len1 = S, lo2 = 0, len2 = S;
+    while (len1 > 1 || len2 > 1) {
+      const int st1 = (len1 + 31) >> 5, st2 = (len2 + 31) >> 5;
+      const bool le1 = len1 > 1 && lane * st1 < len1 && T.loB[lo1 + lane * st1] <= q1;
+      const bool le2 = len2 > 1 && lane * st2 < len2 && T.loB[lo2 + lane * st2] <= q2;
+      const unsigned b1 = __ballot_sync(kFull, le1), b2 = __ballot_sync(kFull, le2);
+      if (len1 > 1) {
+        const int L = b1 ? 31 - __clz(b1) : 0;
+        lo1 += L * st1;
+        len1 = min(st1, len1 - L * st1);
+      }
+      if (len2 > 1) {
+        const int L = b2 ? 31 - __clz(b2) : 0;
+        lo2 += L * st2;
+        len2 = min(st2, len2 - L * st2);
+      }
+    }
+    id1 = T.B[lo1];
+    id2 = T.B[lo2];
+    const Seg s1 = T.sg[id1], s2 = T.sg[id2];
+    t1 = s1.off + (s1.rev ? s1.lo + s1.len - 1 - q1 : q1 - s1.lo);
+    t2 = s2.off + (s2.rev ? s2.lo + s2.len - 1 - q2 : q2 - s2.lo);
+    if ((unsigned)t1 >= (unsigned)n) t1 = 0;
+    if ((unsigned)t2 >= (unsigned)n) t2 = 0;
   }
   __device__ __forceinline__ int at(int t) const {
     const int r = bsearch_le(T.offA, *T.S, t);
@@ -458,16 +498,29 @@ struct SegTour {
   // (the array rule, entry for entry).  false: the table is full.
   __device__ __noinline__ bool flip(int x, int y, LsStats& St) {
     const int lane = lane_id();
-    int i = pos_of_w(x), j = pos_of_w(y);
+    int px, hx, py, hy;
+    pos_id2_w(x, y, px, hx, py, hy);
+    // the position after y and the segment that holds it: y's own, unless
+    // y ends it (then the next one in ant order)
+    const int cy = (py + 1 == n) ? 0 : py + 1;
+    int hcy = hy;
+    if (cy != 0) {
+      const Seg sy = T.sg[hy];
+      if (cy >= sy.off + sy.len) hcy = T.A[T.rankA[hy] + 1];
+    }
     __syncwarp();  // every lane has read the table before any lane rewrites a segment
+    // the span i..j and the segments holding its cuts i and j1 = j + 1
+    // (positions 0 and n need no cut): x..y, or y+1..x-1
+    int i = px, j = py, hi = hx, j1 = cy, hj = hcy;
     int L = j - i;
     if (L < 0) L += n;
     L += 1;
     if (2 * L > n) {
-      const int i2 = (j + 1 == n) ? 0 : j + 1;
-      const int j2 = (i == 0) ? n - 1 : i - 1;
-      i = i2;
-      j = j2;
+      i = cy;
+      hi = hcy;
+      j = (px == 0) ? n - 1 : px - 1;
+      j1 = px;
+      hj = hx;
       L = n - L;
     }
     if (L <= 1) {
@@ -478,12 +531,20 @@ struct SegTour {
     // refuse before touching the table, which then still holds the tour
     if (*T.S + 3 > T.cap) return false;
     St.flip += L;
-    const int j1 = (j + 1 == n) ? 0 : j + 1;
-    if (i != 0 && !seg_split(T, i)) return false;
-    if (j1 != 0 && !seg_split(T, j1)) return false;
+    int si = -1, sj = -1;  // the segments that start at i and at j1
+    if (i != 0) {
+      si = seg_split(T, i, hi);
+      if (si < 0) return false;
+      // both cuts in one segment: the part from i on now holds j1
+      if (hj == hi && si != hi && j1 >= i) hj = si;
+    }
+    if (j1 != 0) {
+      sj = seg_split(T, j1, hj);
+      if (sj < 0) return false;
+    }
     const int S = *T.S;
-    const int ri = bsearch_le_warp(T.offA, S, i);
-    const int rj = (j1 == 0) ? S - 1 : bsearch_le_warp(T.offA, S, j1) - 1;
+    const int ri = (i == 0) ? 0 : T.rankA[si];
+    const int rj = (j1 == 0) ? S - 1 : T.rankA[sj] - 1;
     if (i <= j) {
       // contiguous ranks ri..rj: new off = i + j + 1 - off - len, direction
       // flips, and the ranks reverse.  Lane m takes the pair of ranks
@@ -556,7 +617,7 @@ struct SegTour {
         const int id = T.tmp[straddle];
         const Seg s = T.sg[id];
         nid = S;
-        const int rb = bsearch_le_warp(T.loB, S, s.lo);
+        const int rb = T.rankB[id];
         __syncwarp();
         if (lane == 0) {
           // id keeps ant positions [s.off, n); nid takes [0, s.len - cut)
