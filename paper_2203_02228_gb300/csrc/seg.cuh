@@ -163,18 +163,31 @@ __device__ __forceinline__ int bsearch_le_warp(const int32_t* key, int S, int v)
   return lo;
 }
 
-// Insert val at index r of arr[0..S) (warp-collective).
-__device__ __forceinline__ void u16_insert(uint16_t* arr, int S, int r, uint16_t val) {
+// Insert id (source start lo) at index r of B/loB, arrays of S entries;
+// rankB follows (warp-collective).
+__device__ __forceinline__ void ins_B(const SegTab& T, int S, int r, int id, int32_t lo) {
   const int lane = lane_id();
   for (int e = S - 1; e >= r; e -= 32) {
     const int idx = e - lane;
     uint16_t v = 0;
-    if (idx >= r) v = arr[idx];
+    int32_t k = 0;
+    if (idx >= r) {
+      v = T.B[idx];
+      k = T.loB[idx];
+    }
     __syncwarp();
-    if (idx >= r) arr[idx + 1] = v;
+    if (idx >= r) {
+      T.B[idx + 1] = v;
+      T.loB[idx + 1] = k;
+      T.rankB[v] = (uint16_t)(idx + 1);
+    }
     __syncwarp();
   }
-  if (lane == 0) arr[r] = val;
+  if (lane == 0) {
+    T.B[r] = (uint16_t)id;
+    T.loB[r] = lo;
+    T.rankB[id] = (uint16_t)r;
+  }
   __syncwarp();
 }
 
@@ -338,32 +351,6 @@ static __device__ __noinline__ void seg_merge_at(const SegTab& T, int r) {
   }
   if (lane_id() == 0) *T.S = S - 1;
   __syncwarp();
-}
-
-// Merge ant-adjacent segments that continue each other in the source
-// (never across ant position 0), one pair at a time by seg_merge_at; keys
-// are current on entry and on exit.  A merge at rank r makes no pair
-// before r mergeable, so the scan resumes at r.
-static __device__ __noinline__ void seg_merge_all(const SegTab& T) {
-  const int lane = lane_id();
-  int from = 0;
-  for (;;) {
-    const int S = *T.S;
-    int found = -1;
-    for (int r0 = from; r0 + 1 < S && found < 0; r0 += 32) {
-      const int r = r0 + lane;
-      bool m = false;
-      if (r + 1 < S) {
-        const Seg a = T.sg[T.A[r]], b = T.sg[T.A[r + 1]];
-        m = a.rev == b.rev && (a.rev ? (b.lo + b.len == a.lo) : (a.lo + a.len == b.lo));
-      }
-      const unsigned bal = __ballot_sync(kFull, m);
-      if (bal) found = r0 + __ffs(bal) - 1;
-    }
-    if (found < 0) break;
-    seg_merge_at(T, found);
-    from = found;
-  }
 }
 
 // Tour over the segment table (nodes = source positions).
@@ -631,7 +618,13 @@ struct SegTour {
           }
         }
         __syncwarp();
-        u16_insert(T.B, S, s.rev ? rb : rb + 1, (uint16_t)nid);
+        if (!s.rev) {
+          ins_B(T, S, rb + 1, nid, s.lo + cut);
+        } else {  // nid keeps the low end: it goes before id, whose lo moved up
+          ins_B(T, S, rb, nid, s.lo);
+          if (lane == 0) T.loB[rb + 1] = s.lo + s.len - cut;
+          __syncwarp();
+        }
         S2 = S + 1;
       }
       // new A: [nid] + wrapped part of R + middle A[clo..ri) + unwrapped part of R
@@ -648,14 +641,36 @@ struct SegTour {
       for (int m = lane; m < mid; m += 32) out[head + nlo + m] = T.A[clo + m];
       for (int m = lane; m < nhi; m += 32) out[head + nlo + mid + m] = T.tmp[m];
       __syncwarp();
-      for (int m = lane; m < S2; m += 32) T.A[m] = out[m];
+      for (int m = lane; m < S2; m += 32) {
+        const int id = out[m];
+        T.A[m] = (uint16_t)id;
+        T.offA[m] = T.sg[id].off;
+        T.rankA[id] = (uint16_t)m;
+      }
       __syncwarp();
       if (lane == 0) *T.S = S2;
       __syncwarp();
-      segtab_keys(T);
+      // Merges: reversing a run of segments keeps every pair inside it as
+      // (un)mergeable as it was, and the table held no mergeable pair except
+      // across position 0.  New pairs: the span's right end with the middle
+      // (r1), the middle with the span's left end (r2), and the pair that
+      // crossed position 0 (R[clo-1], R[clo]), now inside the span (r3; none
+      // when the new cut at position 0 falls between them).  Highest rank
+      // first, so that no merge moves a rank still to be merged.
+      const int r1 = head + nlo - 1, r2 = r1 + mid;
+      int r3 = -1;
+      if (clo < nhi)
+        r3 = r2 + clo;  // both in the part placed from position i
+      else if (clo - 1 >= nhi)
+        r3 = head + clo - 1 - nhi;  // both in the part wrapped below position i
+      else if (head)
+        r3 = 0;  // the cut split R[clo-1]: its tail (nid) precedes R[clo]
+      if (r3 > r2) seg_merge_at(T, r3);
+      seg_merge_at(T, r2);
+      seg_merge_at(T, r1);
+      if (r3 >= 0 && r3 < r1) seg_merge_at(T, r3);
+      return true;
     }
-    seg_merge_all(T);
-    return true;
   }
 };
 
