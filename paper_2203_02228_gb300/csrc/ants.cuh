@@ -151,7 +151,9 @@ __device__ __forceinline__ int64_t run_sum(const Colony& C, int first, int dir, 
 // warp 0 posts the request (cmd 1, the current source position), the other
 // warps wait for it at a block barrier; cmd 0 ends their loop.
 struct FbBlock {
-  int cmd, pc;
+  int cmd, pc;             // cmd 1: nearest unvisited of pc; 2: speculative roulette steps
+  int dir, kf;             // cmd 2: direction and tour length at pc
+  int stop[32], sany[32], sq[32];  // cmd 2, per warp: first step that does not follow, its roulette
   uint64_t key[2][32];   // per warp, by ring parity
   int32_t idx[2][32];
   int32_t hdl[2][32];
@@ -511,16 +513,18 @@ __device__ __forceinline__ void place_step(const Colony& C, int32_t* route, int3
   W.pc = q;
 }
 
-// Up to `nspec` roulette steps, lane t taking the step at pc + t*dir.
+// The roulette of the step taken o steps after source position pc (tour
+// length kf there), in a walk along the source in direction dir, on the
+// assumption that the o steps before it follow the source: the nodes they
+// visit count as visited.  valid: the step exists.  Returns whether it
+// picks the source successor; any: some candidate is unvisited, q: the pick.
 template <int KW>
-__device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
-                                          int32_t* chk, Walk& W, int nspec, uint32_t ant,
-                                          uint32_t iter, FbBlock* fb) {
-  const int n = C.n, lane = lane_id();
-  const bool valid = lane < nspec && W.kf + lane < n;
-  const int pt = wrapn(W.pc + lane * W.dir, n);
-  bool any = false;
-  int q = -1;
+__device__ __forceinline__ bool spec_step(const Colony& C, const uint32_t* vis, int pc, int dir, int kf, int o,
+                                          bool valid, uint32_t ant, uint32_t iter, bool& any, int& q) {
+  const int n = C.n;
+  const int pt = wrapn(pc + o * dir, n);
+  any = false;
+  q = -1;
   if (valid) {
     float w[KW];
     int c[KW];
@@ -538,23 +542,80 @@ __device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32
       bool seen = c[s] < 0;
       if (!seen) {
         seen = vis_get(vis, c[s]);
-        if (!seen && W.dir != 0) {
-          int off = (c[s] - W.pc) * W.dir;
+        if (!seen && dir != 0) {
+          int off = (c[s] - pc) * dir;
           if (off < 0) off += n;
-          seen = off >= 1 && off <= lane;  // visited earlier in this speculative run
+          seen = off >= 1 && off <= o;  // visited earlier in this speculative run
         }
       }
       if (seen) w[s] = 0.0f;
       any |= w[s] > 0.0f;
     }
     if (any) {
-      const float u = u01(draw(C.seed, (uint32_t)(W.kf + lane), ant, iter, 0));
+      const float u = u01(draw(C.seed, (uint32_t)(kf + o), ant, iter, 0));
       q = c[roulette<KW>(w, u)];
     }
   }
-  const bool follows = valid && any && W.dir != 0 && q == wrapn(pt + W.dir, n);
-  const unsigned stop = __ballot_sync(kFull, !follows);
-  const int f = stop ? __ffs(stop) - 1 : 32;
+  return valid && any && dir != 0 && q == wrapn(pt + dir, n);
+}
+
+// cmd 2 with the whole block: warp w takes the steps 32w .. 32w+31 after
+// fb.pc and records the first one that does not follow the source.  Must
+// be called by every thread of the block.
+template <int KW>
+__device__ __forceinline__ void block_spec(const Colony& C, const uint32_t* vis, FbBlock& fb, uint32_t ant,
+                                           uint32_t iter) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o = w * 32 + lane;
+  bool any;
+  int q;
+  const bool fol = spec_step<KW>(C, vis, fb.pc, fb.dir, fb.kf, o, fb.kf + o < C.n, ant, iter, any, q);
+  const unsigned stop = __ballot_sync(kFull, !fol);
+  const int l = stop ? __ffs(stop) - 1 : 0;
+  const int anyl = __shfl_sync(kFull, (int)any, l), ql = __shfl_sync(kFull, q, l);
+  if (lane == 0) {
+    fb.stop[w] = stop ? l : 32;
+    fb.sany[w] = anyl;
+    fb.sq[w] = ql;
+  }
+  __syncthreads();
+}
+
+// Up to `nspec` roulette steps, lane t taking the step at pc + t*dir; with
+// the block (fb) and a known direction, up to 32 steps per warp.
+template <int KW>
+__device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
+                                          int32_t* chk, Walk& W, int nspec, uint32_t ant,
+                                          uint32_t iter, FbBlock* fb) {
+  const int n = C.n, lane = lane_id();
+  int f, anyf, qf;
+  if (fb && W.dir != 0 && nspec == 32) {
+    const int nw = blockDim.x >> 5;
+    nspec = 32 * nw;
+    if (lane == 0) {
+      fb->cmd = 2;
+      fb->pc = W.pc;
+      fb->dir = W.dir;
+      fb->kf = W.kf;
+    }
+    __syncwarp();
+    __syncthreads();  // the other warps take their share
+    block_spec<KW>(C, vis, *fb, ant, iter);
+    int ws = 0;
+    while (ws < nw && fb->stop[ws] == 32) ++ws;
+    f = ws < nw ? 32 * ws + fb->stop[ws] : nspec;
+    anyf = ws < nw ? fb->sany[ws] : 0;
+    qf = ws < nw ? fb->sq[ws] : -1;
+  } else {
+    bool any;
+    int q;
+    const bool follows = spec_step<KW>(C, vis, W.pc, W.dir, W.kf, lane, lane < nspec && W.kf + lane < n, ant,
+                                       iter, any, q);
+    const unsigned stop = __ballot_sync(kFull, !follows);
+    f = stop ? __ffs(stop) - 1 : 32;
+    anyf = __shfl_sync(kFull, (int)any, f & 31);
+    qf = __shfl_sync(kFull, q, f & 31);
+  }
   if (f > 0) {
     place_run(C, route, pos, W, W.dir, f);
     vis_set_run(vis, n, W.pc, W.dir, f);
@@ -564,8 +625,6 @@ __device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32
     W.aco += f;
   }
   if (f < nspec && W.kf < n) {
-    const int anyf = __shfl_sync(kFull, (int)any, f);
-    int qf = __shfl_sync(kFull, q, f);
     if (!anyf) qf = fallback_pick(C, vis, W.pc, W, fb);
     W.aco++;
     place_step(C, route, pos, vis, chk, W, qf);
@@ -573,8 +632,9 @@ __device__ __forceinline__ void aco_steps(const Colony& C, int32_t* route, int32
 }
 
 // Focused construction of one ant.  Returns the tour length.
-// fb: the block's fallback state when the whole block helps with nearest-
-// unvisited searches (the caller then posts cmd 0 when it is done), or null.
+// fb: the block's shared state when the whole block helps with nearest-
+// unvisited searches and speculative roulette steps (the caller then posts
+// cmd 0 when it is done), or null.
 template <int KW>
 __device__ __forceinline__ int64_t construct(const Colony& C, int32_t* route, int32_t* pos, uint32_t* vis,
                                              int32_t* chk, Walk& W, uint32_t ant, uint32_t iter,
