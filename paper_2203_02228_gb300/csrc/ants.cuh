@@ -154,159 +154,60 @@ struct FbBlock {
   int cmd, pc;             // cmd 1: nearest unvisited of pc; 2: speculative roulette steps
   int dir, kf;             // cmd 2: direction and tour length at pc
   int stop[32], sany[32], sq[32];  // cmd 2, per warp: first step that does not follow, its roulette
-  uint64_t key[2][32];   // per warp, by ring parity
-  int32_t idx[2][32];
-  int32_t hdl[2][32];
+  uint64_t key[32];      // cmd 1, per warp: nearest unvisited (squared distance, node id)
+  int32_t idx[32];
 };
 
 // The nearest unvisited node of source position fb.pc by (squared
-// distance, node id), with every warp of the block: the cells of each
-// grid ring are split over the warps (a warp takes 32 cells and spreads
-// their points over its lanes), the block's minimum closes each ring, and
-// the ring search stops by the same exact rule as ring_nearest; if 24
-// rings do not settle it, the visited words are split over all threads.
-// Must be called by every thread of the block; returns the source position
-// (the same on every thread).
+// distance, node id), with every thread of the block: the visited words
+// are split over the threads, each unvisited position is measured, and
+// the block's minimum wins.  (A search over grid rings around fb.pc, one
+// barrier per ring, took 11-14 rings on average at the points where
+// construction needs this search -- late in the walk, with few nodes left
+// -- and cost several times the scan.)  Must be called by every thread of
+// the block; returns the source position (the same on every thread).
 __device__ __noinline__ int block_nearest(const Colony& C, const uint32_t* vis, FbBlock& fb) {
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int n = C.n;
   const int pc = fb.pc;
   const int2 xu = C.XYsrc[pc];
-  const Grid& g = C.grid;
-  const int cx = (xu.x - g.minx) / g.cs, cy = (xu.y - g.miny) / g.cs;
-  uint64_t best_k = ~0ull;  // block-wide best so far (uniform)
-  int32_t best_i = INT_MAX;
-  int best_h = -1;
-  constexpr int kRings = 24;
-  for (int r = 0; r <= kRings; ++r) {
-    const int cnt = r == 0 ? 1 : 8 * r;
-    uint64_t bk = ~0ull;
-    int32_t bi = INT_MAX;
-    int bh = -1;
-    for (int c0 = 32 * w; c0 < cnt; c0 += 32 * nw) {
-      const int c = c0 + lane;
-      int st = 0, len = 0;
-      if (c < cnt) {
-        int dx = 0, dy = 0;
-        if (r > 0) {
-          if (c <= 2 * r) {
-            dx = c - r;
-            dy = -r;
-          } else if (c <= 4 * r + 1) {
-            dx = c - (3 * r + 1);
-            dy = r;
-          } else if (c <= 6 * r) {
-            dx = -r;
-            dy = c - (5 * r + 1);
-          } else {
-            dx = r;
-            dy = c - 7 * r;
-          }
-        }
-        const int x = cx + dx, y = cy + dy;
-        if (x >= 0 && x < g.gx && y >= 0 && y < g.gy) {
-          const int cell = y * g.gx + x;
-          st = C.cell_start[cell];
-          len = C.cell_start[cell + 1] - st;
-        }
-      }
-      int incl = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int total = __shfl_sync(kFull, incl, 31);
-      const int excl_st = st - (incl - len);
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        int o = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (__shfl_sync(kFull, incl, o + step - 1) <= t) o += step;
-        const int base = __shfl_sync(kFull, excl_st, o);
-        const int4 P = t < total ? C.cell_src[base + t] : make_int4(-1, 0, 0, INT_MAX);
-        if (P.x >= 0 && !vis_get(vis, P.x)) {
-          const uint64_t m = sqdist(xu, make_int2(P.y, P.z));
-          if (m < bk || (m == bk && P.w < bi)) {
-            bk = m;
-            bi = P.w;
-            bh = P.x;
-          }
-        }
-      }
-    }
-    uint64_t wk = bk;
-    int32_t wi = bi;
-    warp_min_key(wk, wi);
-    const unsigned own = __ballot_sync(kFull, bi == wi && bk == wk && wi != INT_MAX);
-    const int wh = own ? __shfl_sync(kFull, bh, __ffs(own) - 1) : -1;
-    const int par = r & 1;
-    if (lane == 0) {
-      fb.key[par][w] = wk;
-      fb.idx[par][w] = wi;
-      fb.hdl[par][w] = wh;
-    }
-    __syncthreads();
-    for (int v = 0; v < nw; ++v) {
-      const uint64_t k2 = fb.key[par][v];
-      const int32_t i2 = fb.idx[par][v];
-      if (k2 < best_k || (k2 == best_k && i2 < best_i)) {
-        best_k = k2;
-        best_i = i2;
-        best_h = fb.hdl[par][v];
-      }
-    }
-    const bool lin = cx - r <= 0, rin = cx + r >= g.gx - 1, din = cy - r <= 0, uin = cy + r >= g.gy - 1;
-    bool done = lin && rin && din && uin;
-    if (!done && best_i != INT_MAX) {
-      int64_t dmin = INT64_MAX;
-      if (!lin) dmin = min(dmin, (int64_t)xu.x - ((int64_t)g.minx + (int64_t)(cx - r) * g.cs) + 1);
-      if (!rin) dmin = min(dmin, ((int64_t)g.minx + (int64_t)(cx + r + 1) * g.cs) - xu.x);
-      if (!din) dmin = min(dmin, (int64_t)xu.y - ((int64_t)g.miny + (int64_t)(cy - r) * g.cs) + 1);
-      if (!uin) dmin = min(dmin, ((int64_t)g.miny + (int64_t)(cy + r + 1) * g.cs) - xu.y);
-      done = best_k < (uint64_t)(dmin * dmin);
-    }
-    if (done && best_i != INT_MAX) return best_h;
-    if (done) break;  // every cell scanned and nothing unvisited: cannot happen while a node is unvisited
-  }
-  // every unvisited position, the visited words split over the block; the
-  // barrier keeps this phase's slot writes after every thread's reads of
-  // the last ring's slots
-  __syncthreads();
   uint64_t bk = ~0ull;
   int32_t bi = INT_MAX;
   const int words = (n + 31) >> 5;
-  for (int wi2 = tid; wi2 < words; wi2 += blockDim.x) {
-    uint32_t fr = ~vis[wi2];
-    if (wi2 == words - 1 && (n & 31)) fr &= (1u << (n & 31)) - 1u;
+  for (int wi = tid; wi < words; wi += blockDim.x) {
+    uint32_t fr = ~vis[wi];
+    if (wi == words - 1 && (n & 31)) fr &= (1u << (n & 31)) - 1u;
     while (fr) {
-      const int q = wi2 * 32 + __ffs(fr) - 1;
+      const int q = wi * 32 + __ffs(fr) - 1;
       fr &= fr - 1;
       const uint64_t m = sqdist(xu, C.XYsrc[q]);
-      const int32_t nd = C.src_route[q];
-      if (m < bk || (m == bk && nd < bi)) {
-        bk = m;
-        bi = nd;
+      if (m <= bk) {  // the node id only decides ties
+        const int32_t nd = C.src_route[q];
+        if (m < bk || nd < bi) {
+          bk = m;
+          bi = nd;
+        }
       }
     }
   }
   warp_min_key(bk, bi);
   if (lane == 0) {
-    fb.key[0][w] = bk;
-    fb.idx[0][w] = bi;
+    fb.key[w] = bk;
+    fb.idx[w] = bi;
   }
   __syncthreads();
-  best_k = ~0ull;
-  best_i = INT_MAX;
+  uint64_t best_k = ~0ull;
+  int32_t best_i = INT_MAX;
   for (int v = 0; v < nw; ++v) {
-    const uint64_t k2 = fb.key[0][v];
-    const int32_t i2 = fb.idx[0][v];
+    const uint64_t k2 = fb.key[v];
+    const int32_t i2 = fb.idx[v];
     if (k2 < best_k || (k2 == best_k && i2 < best_i)) {
       best_k = k2;
       best_i = i2;
     }
   }
+  // (the next request reaches the slots only after the barrier that posts
+  // it, which every thread passes after these reads)
   if (best_i < 0 || best_i >= n) {  // cannot happen while a node is unvisited
     if (tid == 0) atomicOr(&C.st->error, kErrInternal);
     return pc == 0 ? n - 1 : pc - 1;
