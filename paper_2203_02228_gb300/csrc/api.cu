@@ -63,9 +63,10 @@ struct faco_ctx {
 // best tour, source, rows, prefix sums; one fewer without segment tables.
 constexpr int kItersKernels = 7;
 // Kernels of the set-up: bbox, cell count, cell scan, cell fill, kNN,
-// nearest-neighbour tour, positions, initial local search, tour length,
-// state, positions (source), positions (best), rows, prefix sums.
-constexpr int kSetupKernels = 14;
+// nearest-neighbour tour, positions, relabel, initial local search,
+// unlabel, tour length, state, positions (source), positions (best), rows,
+// prefix sums.
+constexpr int kSetupKernels = 16;
 
 namespace {
 
@@ -283,18 +284,31 @@ int create_common(const int32_t* coords, int32_t n, int32_t k, const faco_params
     }
     int32_t *q = nullptr, *lg = nullptr;
     uint8_t* fl = nullptr;
+    // the search runs on copies named by nearest-neighbour tour position
+    int2* xy_t = nullptr;
+    int32_t *cand_t = nullptr, *dcand_t = nullptr, *route_t = nullptr, *pos_t = nullptr;
+    const size_t nk = (size_t)n * c->k;
     if ((r2 = dalloc(tmp, &q, n)) != FACO_OK || (r2 = dalloc(tmp, &lg, n)) != FACO_OK ||
-        (r2 = dalloc(tmp, &fl, n)) != FACO_OK) {
+        (r2 = dalloc(tmp, &fl, n)) != FACO_OK || (r2 = dalloc(tmp, &xy_t, n)) != FACO_OK ||
+        (r2 = dalloc(tmp, &cand_t, nk)) != FACO_OK || (r2 = dalloc(tmp, &dcand_t, nk)) != FACO_OK ||
+        (r2 = dalloc(tmp, &route_t, n)) != FACO_OK || (r2 = dalloc(tmp, &pos_t, n)) != FACO_OK) {
       free_tmp();
       return r2;
     }
     cudaError_t e = launch_nn_tour(c->xy, n, c->cand, c->k, c->backup, c->bl, c->init_route, vis_g, g,
                                    c->cell_start, c->cell_src, s);
     if (e == cudaSuccess) e = launch_positions(c->init_route, c->src_pos, n, s);
+    if (e == cudaSuccess)
+      e = launch_relabel(c->init_route, c->src_pos, c->xy, c->cand, c->dcand, n, c->k, xy_t, cand_t, dcand_t,
+                         route_t, pos_t, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fl, 0, n, s);
     if (e == cudaSuccess)
-      e = launch_init_ls(c->xy, n, c->cand, c->dcand, c->k, prm.oropt, prm.verify_pass, prm.init_3opt,
-                         c->init_route, c->src_pos, q, fl, lg, s);
+      e = launch_init_ls(xy_t, n, cand_t, dcand_t, c->k, prm.oropt, prm.verify_pass, prm.init_3opt, route_t, pos_t,
+                         q, fl, lg, s);
+    // back to node ids (through tmp_route: init_route is the map's source)
+    if (e == cudaSuccess) e = launch_unlabel(c->init_route, route_t, c->tmp_route, n, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->init_route, c->tmp_route, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = launch_tour_length(c->xy, c->init_route, n, c->len_tmp, s);
     Colony C = colony_view(c);
     if (e == cudaSuccess) e = launch_state_init(C, c->len_tmp, s);

@@ -76,6 +76,13 @@ cudaError_t build_lists_batch(const Colony* cols, const ColonySetup* sets, int c
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
                            int bl, int32_t* route, uint32_t* vis_g, const Grid& g, const int32_t* cstart,
                            const int4* recs, cudaStream_t s);
+// Copies of the coordinates and lists named by nearest-neighbour tour
+// position (route0, pos0: that tour and its inverse) with the identity tour
+// in route_t/pos_t; and the searched tour mapped back to node ids.
+cudaError_t launch_relabel(const int32_t* route0, const int32_t* pos0, const int2* xy, const int32_t* cand,
+                           const int32_t* dcand, int n, int k, int2* xy_t, int32_t* cand_t, int32_t* dcand_t,
+                           int32_t* route_t, int32_t* pos_t, cudaStream_t s);
+cudaError_t launch_unlabel(const int32_t* route0, const int32_t* route_t, int32_t* route, int n, cudaStream_t s);
 cudaError_t launch_init_ls(const int2* xy, int n, const int32_t* cand, const int32_t* dcand, int k, int oropt,
                            int verify, int init3, int32_t* route, int32_t* pos, int32_t* queue, uint8_t* flags,
                            int32_t* logb, cudaStream_t s);

@@ -515,6 +515,39 @@ __global__ void k_tests(int what, const void* in, void* out, int count, int widt
   }
 }
 
+// The initial search names nodes by their position in the nearest-
+// neighbour tour: node i of the copies is route0[i], and a candidate list
+// names its entries the same way.  Lists keep their order and coordinates
+// their values, so every decision of the search is the same; what changes is
+// where things lie in memory -- consecutive names are neighbours on the walk,
+// so a node's coordinates, lists and tour neighbours share cache lines with
+// those of the nodes around it.  One thread per list entry.
+__global__ void k_relabel(const int32_t* __restrict__ route0, const int32_t* __restrict__ pos0,
+                          const int2* __restrict__ xy, const int32_t* __restrict__ cand,
+                          const int32_t* __restrict__ dcand, int n, int k, int2* __restrict__ xy_t,
+                          int32_t* __restrict__ cand_t, int32_t* __restrict__ dcand_t,
+                          int32_t* __restrict__ route_t, int32_t* __restrict__ pos_t) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * k) return;
+  const int i = (int)(e / k), s = (int)(e - (size_t)i * k);
+  const int u = route0[i];
+  const int c = cand[(size_t)u * k + s];
+  cand_t[e] = c >= 0 ? pos0[c] : c;
+  dcand_t[e] = dcand[(size_t)u * k + s];
+  if (s == 0) {
+    xy_t[i] = xy[u];
+    route_t[i] = i;
+    pos_t[i] = i;
+  }
+}
+
+// route[t] = route0[route_t[t]]: the searched tour back in node ids.
+__global__ void k_unlabel(const int32_t* __restrict__ route0, const int32_t* __restrict__ route_t,
+                          int32_t* __restrict__ route, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) route[t] = route0[route_t[t]];
+}
+
 }  // namespace
 
 cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, const int32_t* backup,
@@ -526,6 +559,20 @@ cudaError_t launch_nn_tour(const int2* xy, int n, const int32_t* cand, int k, co
     if (e != cudaSuccess) return e;
   }
   k_nn_tour<<<1, 32, smem, s>>>(xy, n, cand, k, backup, bl, route, vis_g, g, cstart, recs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(const int32_t* route0, const int32_t* pos0, const int2* xy, const int32_t* cand,
+                           const int32_t* dcand, int n, int k, int2* xy_t, int32_t* cand_t, int32_t* dcand_t,
+                           int32_t* route_t, int32_t* pos_t, cudaStream_t s) {
+  const size_t e = (size_t)n * k;
+  k_relabel<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(route0, pos0, xy, cand, dcand, n, k, xy_t, cand_t, dcand_t,
+                                                        route_t, pos_t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unlabel(const int32_t* route0, const int32_t* route_t, int32_t* route, int n, cudaStream_t s) {
+  k_unlabel<<<(n + 255) / 256, 256, 0, s>>>(route0, route_t, route, n);
   return cudaGetLastError();
 }
 
