@@ -365,7 +365,6 @@ __device__ __forceinline__ int64_t eval_or3(const Tour& T, int a, int mv[6]) {
     const int dir = idx >= kk ? 1 : 0;
     const int r = idx - dir * kk;
     const int i = r / k, j = r - i * k;
-    const int t2 = dir ? p : s1;
     const int2 xt2 = dir ? xp : xs;
     const int g1 = (dir ? d_ap : d_as) - T.cdist(a, i);
     if (g1 <= 0) continue;
