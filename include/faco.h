@@ -42,7 +42,9 @@ enum {
   FACO_E_SIZE = -2,      /* caller buffer too small                       */
   FACO_E_NOMEM = -3,     /* device or host allocation failed              */
   FACO_E_CUDA = -4,      /* CUDA runtime error (no device, launch, fault) */
-  FACO_E_TIMEOUT = -5,   /* a bounded device-side wait gave up            */
+  FACO_E_TIMEOUT = -5,   /* a bounded device-side wait gave up; reserved: */
+                         /* no kernel of this version waits on the       */
+                         /* device, so no call returns it                */
   FACO_E_STATE = -6,     /* call not valid in the context's state         */
   FACO_E_CAPACITY = -7   /* a fixed device capacity was exceeded          */
 };
@@ -135,7 +137,8 @@ int faco_create_device(const int32_t* coords_xy, int32_t n, int32_t k, const fac
 int faco_iterate(faco_ctx* c, int32_t ants, int32_t budget);
 
 /* Synchronises the context's stream and reports device-side error flags.
- * Errors: FACO_E_CUDA, FACO_E_CAPACITY, FACO_E_TIMEOUT. */
+ * Errors: FACO_E_CUDA, FACO_E_CAPACITY (FACO_E_TIMEOUT is reserved for a
+ * bounded device wait; no kernel of this version has one). */
 int faco_sync(faco_ctx* c);
 
 /* Copies the global-best tour (host array of len >= n node ids) and its

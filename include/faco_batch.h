@@ -66,8 +66,9 @@ int faco_batch_create(const int32_t* const* coords_xy, const int32_t* ns, int32_
  * FACO_E_ARG, FACO_E_NOMEM, FACO_E_CUDA. */
 int faco_batch_iterate(faco_batch* b, int32_t ants, int32_t budget);
 
-/* Waits for the enqueued work; FACO_E_TIMEOUT / FACO_E_CAPACITY / FACO_E_CUDA
- * when a colony raised a device error flag. */
+/* Waits for the enqueued work; FACO_E_CAPACITY / FACO_E_CUDA when a colony
+ * raised a device error flag (FACO_E_TIMEOUT is reserved: no kernel of this
+ * version waits on the device). */
 int faco_batch_sync(faco_batch* b);
 
 /* Global-best tour (ns[i] entries, len >= ns[i]; NULL to skip) and length of
