@@ -216,11 +216,11 @@ int faco_get_ant_stats(faco_ctx* c, int64_t* stats);
  * bl' = 0).  It calls no allocating routine: its scratch (the point grid)
  * is a fixed array inside the library, reserved on every GPU that loads
  * the library until the process exits; n may be at most 262144
- * (FACO_E_SIZE above).  The first call on a device looks up that array's
- * device address, so make it before any stream capture; the address is kept
- * for the life of the process, so this call must not be used on a device
- * after cudaDeviceReset (which unloads the library's module and may place
- * the array elsewhere when it is loaded again).  All calls share
+ * (FACO_E_SIZE above).  Every call looks up that array's device address
+ * afresh, so the call stays valid after a cudaDeviceReset (which unloads
+ * the library's module and may place the array elsewhere when it is loaded
+ * again); it synchronises its stream, so it cannot run inside a stream
+ * capture.  All calls share
  * the array: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The call
  * synchronises `stream` (a cudaStream_t, NULL = legacy default stream)

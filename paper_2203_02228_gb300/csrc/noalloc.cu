@@ -9,7 +9,6 @@
 // builder -- lives in the file-scope array below, reserved once when the
 // library is loaded and kept by every GPU that loads it until exit.
 #include <cmath>
-#include <mutex>
 
 #include "faco.h"
 #include "launch.h"
@@ -28,29 +27,17 @@ constexpr int64_t kScratchInts = 8 + kNoAllocMaxCells + (kNoAllocMaxCells + 1) +
 
 __device__ __align__(256) int32_t g_list_scratch[kScratchInts];
 
-// Device address of g_list_scratch per device, looked up on first use and
-// kept for the life of the process (a cudaDeviceReset would invalidate it;
-// the header says the call is not to be used across one).
-constexpr int kMaxDevices = 64;
-int32_t* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
+// Device address of g_list_scratch on the current device.  Looked up on
+// every call (cheap beside the stream synchronisation the call makes
+// anyway), so that the address stays right after a cudaDeviceReset, which
+// loads the module again, possibly elsewhere.
 int scratch_for_current_device(int32_t** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_list_scratch) != cudaSuccess || !p) {
     (void)cudaGetLastError();
     return FACO_E_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_list_scratch) != cudaSuccess || !p) {
-      (void)cudaGetLastError();
-      return FACO_E_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<int32_t*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<int32_t*>(p);
   return FACO_OK;
 }
 
